@@ -144,6 +144,28 @@ void ora_rate_factors(const ora_network* net, double T9, double rho,
     }
 }
 
+/* species with c_ir != 0 of every reaction (increasing species index), so
+   the sums over r below visit only the reactions that touch a species */
+typedef struct {
+    int cnt;
+    int sp[6];
+    double c[6];
+} rxn_species;
+
+static rxn_species* species_lists(const ora_network* net) {
+    rxn_species* L = calloc((size_t)net->R + 1, sizeof(rxn_species));
+    for (int r = 0; r < net->R; ++r)
+        for (int i = 0; i < net->N; ++i) {
+            double c = stoich(net, i, r);
+            if (c != 0.0) {
+                L[r].sp[L[r].cnt] = i;
+                L[r].c[L[r].cnt] = c;
+                L[r].cnt++;
+            }
+        }
+    return L;
+}
+
 /* R_r = k_r prod over reactant occurrences of Y */
 static void reaction_terms(const ora_network* net, const double* x,
                            const double* k, double* Rr) {
@@ -164,19 +186,16 @@ static double heat_capacity(const ora_network* net, const double* x) {
     return 1.5 * sy + 1e-3 * T9 * T9 * T9;
 }
 
-/* f (n entries) and edot at state x, given k_r for the state's T9 */
-static void rhs_given_k(const ora_network* net, const double* x, const double* k,
+/* f (n entries) and edot at state x, given k_r for the state's T9.
+   f_i = sum_r c_ir R_r, accumulated over r in increasing order. */
+static void rhs_given_k(const ora_network* net, const rxn_species* L,
+                        const double* x, const double* k,
                         double* f, double* edot, double* Rr) {
     int N = net->N, R = net->R;
     reaction_terms(net, x, k, Rr);
-    for (int i = 0; i < N; ++i) {
-        double s = 0.0;
-        for (int r = 0; r < R; ++r) {
-            double c = stoich(net, i, r);
-            if (c != 0.0) s += c * Rr[r];
-        }
-        f[i] = s;
-    }
+    for (int i = 0; i < N; ++i) f[i] = 0.0;
+    for (int r = 0; r < R; ++r)
+        for (int q = 0; q < L[r].cnt; ++q) f[L[r].sp[q]] += L[r].c[q] * Rr[r];
     double ed = 0.0;
     if (net->Q)
         for (int r = 0; r < R; ++r) ed += net->Q[r] * Rr[r];
@@ -202,21 +221,35 @@ static double dterm_dY(const ora_network* net, const double* x, const double* k,
     return v;
 }
 
-/* dense Jacobian J[i*n + j] = d f_i / d x_j at x (k, g for the state's T9) */
-static void jacobian_given_k(const ora_network* net, const double* x,
-                             const double* k, const double* g, double* J,
-                             double* Rr) {
+/* distinct reactant species of reaction r; returns their count */
+static int distinct_reactants(const ora_network* net, int r, int* out) {
+    int m = 0;
+    for (int s = 0; s < 3; ++s) {
+        int j = net->reactants[3 * r + s];
+        if (j < 0) continue;
+        int seen = 0;
+        for (int q = 0; q < m; ++q) seen |= out[q] == j;
+        if (!seen) out[m++] = j;
+    }
+    return m;
+}
+
+/* dense Jacobian J[i*n + j] = d f_i / d x_j at x (k, g for the state's T9):
+   J_ij = sum_r c_ir dR_r/dY_j, accumulated over r in increasing order */
+static void jacobian_given_k(const ora_network* net, const rxn_species* L,
+                             const double* x, const double* k, const double* g,
+                             double* J, double* Rr) {
     int N = net->N, R = net->R, n = N + (net->self_heating ? 1 : 0);
     memset(J, 0, sizeof(double) * n * n);
-    for (int i = 0; i < N; ++i)
-        for (int j = 0; j < N; ++j) {
-            double s = 0.0;
-            for (int r = 0; r < R; ++r) {
-                double c = stoich(net, i, r);
-                if (c != 0.0) s += c * dterm_dY(net, x, k, r, j);
-            }
-            J[i * n + j] = s;
+    for (int r = 0; r < R; ++r) {
+        int js[3];
+        int m = distinct_reactants(net, r, js);
+        for (int a = 0; a < m; ++a) {
+            double d = dterm_dY(net, x, k, r, js[a]);
+            for (int q = 0; q < L[r].cnt; ++q)
+                J[L[r].sp[q] * n + js[a]] += L[r].c[q] * d;
         }
+    }
     if (!net->self_heating) return;
     reaction_terms(net, x, k, Rr);
     double cv = heat_capacity(net, x);
@@ -226,19 +259,17 @@ static void jacobian_given_k(const ora_network* net, const double* x,
         dedT += net->Q[r] * Rr[r] * g[r];
     }
     double fT = ed / cv;
-    for (int i = 0; i < N; ++i) {
-        double s = 0.0;
-        for (int r = 0; r < R; ++r) {
-            double c = stoich(net, i, r);
-            if (c != 0.0) s += c * Rr[r] * g[r];
-        }
-        J[i * n + N] = s;
+    for (int r = 0; r < R; ++r)
+        for (int q = 0; q < L[r].cnt; ++q)
+            J[L[r].sp[q] * n + N] += L[r].c[q] * Rr[r] * g[r];
+    /* T row: d edot / dY_j, accumulated over r in increasing order */
+    for (int r = 0; r < R; ++r) {
+        int js[3];
+        int m = distinct_reactants(net, r, js);
+        for (int a = 0; a < m; ++a)
+            J[N * n + js[a]] += net->Q[r] * dterm_dY(net, x, k, r, js[a]);
     }
-    for (int j = 0; j < N; ++j) {
-        double de = 0.0;
-        for (int r = 0; r < R; ++r) de += net->Q[r] * dterm_dY(net, x, k, r, j);
-        J[N * n + j] = de / cv - fT * 1.5 / cv;
-    }
+    for (int j = 0; j < N; ++j) J[N * n + j] = J[N * n + j] / cv - fT * 1.5 / cv;
     double T9 = x[N];
     J[N * n + N] = dedT / cv - fT * (3e-3 * T9 * T9) / cv;
 }
@@ -251,8 +282,10 @@ void ora_rhs(const ora_network* net, const double* x, double T9, double rho,
              const double* ln_mult, double* f, double* edot) {
     double* k = malloc(sizeof(double) * (net->R + 1));
     double* Rr = malloc(sizeof(double) * (net->R + 1));
+    rxn_species* L = species_lists(net);
     ora_rate_factors(net, net->self_heating ? x[net->N] : T9, rho, ln_mult, k, NULL);
-    rhs_given_k(net, x, k, f, edot, Rr);
+    rhs_given_k(net, L, x, k, f, edot, Rr);
+    free(L);
     free(k);
     free(Rr);
 }
@@ -262,8 +295,10 @@ void ora_jacobian(const ora_network* net, const double* x, double T9, double rho
     double* k = malloc(sizeof(double) * (net->R + 1));
     double* g = malloc(sizeof(double) * (net->R + 1));
     double* Rr = malloc(sizeof(double) * (net->R + 1));
+    rxn_species* L = species_lists(net);
     ora_rate_factors(net, net->self_heating ? x[net->N] : T9, rho, ln_mult, k, g);
-    jacobian_given_k(net, x, k, g, J, Rr);
+    jacobian_given_k(net, L, x, k, g, J, Rr);
+    free(L);
     free(k);
     free(g);
     free(Rr);
@@ -377,6 +412,7 @@ typedef struct {
 } ora_tape;
 
 typedef struct {
+    rxn_species* L;
     double* k; double* g; double* Rr;
     double* J; double* M; int* piv;
     double* f; double* x; double* xp; double* psi; double* d; double* G;
@@ -386,8 +422,10 @@ typedef struct {
     double Eh[HMAX];
 } work_t;
 
-static work_t* work_alloc(int n, int R) {
+static work_t* work_alloc(const ora_network* net) {
+    int n = net->N + (net->self_heating ? 1 : 0), R = net->R;
     work_t* W = calloc(1, sizeof(work_t));
+    W->L = species_lists(net);
     W->k = malloc(sizeof(double) * (R + 1));
     W->g = malloc(sizeof(double) * (R + 1));
     W->Rr = malloc(sizeof(double) * (R + 1));
@@ -403,6 +441,7 @@ static work_t* work_alloc(int n, int R) {
 }
 
 static void work_free(work_t* W) {
+    free(W->L);
     free(W->k); free(W->g); free(W->Rr); free(W->J); free(W->M); free(W->piv);
     free(W->f); free(W->x); free(W->xp); free(W->psi); free(W->d); free(W->G);
     free(W->w); free(W->x1); free(W->f1); free(W->tmp); free(W->xh);
@@ -483,7 +522,7 @@ static int burn_zone(const ora_network* net, const ora_options* opt,
     /* rates, f(x0); with a fixed temperature these rates serve the whole burn */
     rates_for(&z, W->xh, W, 0);
     double ed0;
-    rhs_given_k(net, W->xh, W->k, W->f, &ed0, W->Rr);
+    rhs_given_k(net, W->L, W->xh, W->k, W->f, &ed0, W->Rr);
     cnt[C_RHS]++;
     int finite0 = all_finite(n, W->xh) && all_finite(n, W->f) && T9_0 > 0.0;
     for (int r = 0; r < net->R && finite0; ++r) finite0 = isfinite(W->k[r]);
@@ -504,7 +543,7 @@ static int burn_zone(const ora_network* net, const ora_options* opt,
         if (hp > t_end) hp = t_end;
         for (int i = 0; i < n; ++i) W->x[i] = W->xh[i] + hp * f0[i];
         if (net->self_heating) rates_for(&z, W->x, W, 0);
-        rhs_given_k(net, W->x, W->k, W->f1, NULL, W->Rr);
+        rhs_given_k(net, W->L, W->x, W->k, W->f1, NULL, W->Rr);
         cnt[C_RHS]++;
         for (int i = 0; i < n; ++i) W->tmp[i] = (W->f1[i] - f0[i]) / hp;
         double d2 = wnorm(n, W->tmp, W->w);
@@ -547,7 +586,7 @@ static int burn_zone(const ora_network* net, const ora_options* opt,
         /* Jacobian + f at the predictor, LU of M */
         memcpy(W->x, W->xp, sizeof(double) * n);
         if (net->self_heating) rates_for(&z, W->x, W, 1);
-        jacobian_given_k(net, W->x, W->k, W->g, W->J, W->Rr);
+        jacobian_given_k(net, W->L, W->x, W->k, W->g, W->J, W->Rr);
         cnt[C_JAC]++;
         for (int i = 0; i < n; ++i)
             for (int j = 0; j < n; ++j)
@@ -557,7 +596,7 @@ static int burn_zone(const ora_network* net, const ora_options* opt,
         int converged = 0;
         for (int m = 0; ok && m < opt->newton_maxit; ++m) {
             if (m > 0 && net->self_heating) rates_for(&z, W->x, W, 0);
-            rhs_given_k(net, W->x, W->k, W->f, NULL, W->Rr);
+            rhs_given_k(net, W->L, W->x, W->k, W->f, NULL, W->Rr);
             cnt[C_RHS]++;
             for (int i = 0; i < n; ++i)
                 W->G[i] = alpha[0] * W->x[i] + W->psi[i] - h * W->f[i];
@@ -668,8 +707,7 @@ typedef struct {
 static void* batch_worker(void* arg) {
     batch_t* B = arg;
     const ora_network* net = B->net;
-    int n = state_dim(net);
-    work_t* W = work_alloc(n, net->R);
+    work_t* W = work_alloc(net);
     for (;;) {
         long z = atomic_fetch_add(&B->next, 1);
         if (z >= B->Z) break;
@@ -716,8 +754,7 @@ int ora_burn_tape(const ora_network* net, const ora_options* opt,
                   double* Y, double* T9_out, double* E, int32_t* cnt,
                   int32_t cap, double* tape_t, int32_t* tape_k, double* tape_x,
                   double* tape_E, int32_t* tape_count) {
-    int n = state_dim(net);
-    work_t* W = work_alloc(n, net->R);
+    work_t* W = work_alloc(net);
     ora_tape tp = {cap, tape_t, tape_k, tape_x, tape_E, 0};
     int st = burn_zone(net, opt, Y0, T9_0, rho, ln_mult, Y, T9_out, E, cnt, &tp, W);
     *tape_count = tp.count;
@@ -738,7 +775,7 @@ int ora_replay(const ora_network* net, const ora_options* opt, const double* Y0,
                const double* tape_t, const int32_t* tape_k, double tol,
                int32_t maxit, double* x_out, double* E_out) {
     const int N = net->N, n = state_dim(net);
-    work_t* W = work_alloc(n, net->R);
+    work_t* W = work_alloc(net);
     int32_t cnt[C_COUNT] = {0};
     zone_ctx z = {net, rho, T9_0, ln_mult, cnt};
     int nh = 0, rc = 0;
@@ -747,7 +784,7 @@ int ora_replay(const ora_network* net, const ora_options* opt, const double* Y0,
     push_history(W, n, &nh, tape_t[0], W->x1, 0.0);
     rates_for(&z, W->xh, W, 1);
     double* f0 = malloc(sizeof(double) * n);
-    rhs_given_k(net, W->xh, W->k, f0, NULL, W->Rr);
+    rhs_given_k(net, W->L, W->xh, W->k, f0, NULL, W->Rr);
     for (int s = 1; s <= S && rc == 0; ++s) {
         int kk = tape_k[s];
         double t_new = tape_t[s], h = t_new - W->th[0];
@@ -764,8 +801,8 @@ int ora_replay(const ora_network* net, const ora_options* opt, const double* Y0,
         int conv = 0, polish = 0;
         for (int m = 0; m < maxit; ++m) {
             rates_for(&z, W->x, W, 1);
-            jacobian_given_k(net, W->x, W->k, W->g, W->J, W->Rr);
-            rhs_given_k(net, W->x, W->k, W->f, NULL, W->Rr);
+            jacobian_given_k(net, W->L, W->x, W->k, W->g, W->J, W->Rr);
+            rhs_given_k(net, W->L, W->x, W->k, W->f, NULL, W->Rr);
             for (int i = 0; i < n; ++i)
                 for (int j = 0; j < n; ++j)
                     W->M[i * n + j] = (i == j ? alpha[0] : 0.0) - h * W->J[i * n + j];
@@ -808,7 +845,7 @@ int ora_forward_sensitivity(const ora_network* net, double T9_fixed, double rho,
                             double* dx_out, double* dE_out) {
     const int N = net->N, R = net->R, n = state_dim(net);
     const int P = R + n + (net->self_heating ? 0 : 1);
-    work_t* W = work_alloc(n, R);
+    work_t* W = work_alloc(net);
     int32_t cnt[C_COUNT] = {0};
     zone_ctx z = {net, rho, T9_fixed, ln_mult, cnt};
     /* history of sensitivity matrices, newest first */
@@ -828,7 +865,7 @@ int ora_forward_sensitivity(const ora_network* net, double T9_fixed, double rho,
         ora_bdf_alpha(kk, t_new, th, h, alpha);
         const double* x = tape_x + (size_t)s * n;
         rates_for(&z, x, W, 1);
-        jacobian_given_k(net, x, W->k, W->g, W->J, W->Rr);
+        jacobian_given_k(net, W->L, x, W->k, W->g, W->J, W->Rr);
         reaction_terms(net, x, W->k, W->Rr);
         double cv = net->self_heating ? heat_capacity(net, x) : 1.0;
         for (int i = 0; i < n; ++i)
