@@ -1,0 +1,358 @@
+#!/usr/bin/env python
+"""Zone-burns per second of the batched stiff reaction-network burn on GB300.
+
+One step = one burn of the whole workload: every zone of the self-heating
+13-species alpha chain (65,536 zones, T9 log-uniform [0.5, 5], rho
+log-uniform [1e5, 1e8], t_end 1e-3 s, rtol 1e-8, atol 1e-12) integrated by
+the persistent lane-per-zone kernel, inputs already in HBM.  Prints one JSON
+line (rank 0).  ``--impl reference`` times the CPU oracle instead.
+
+Multi-GPU: one process per GPU (torchrun); every rank burns its own zones
+(weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import gen  # noqa: E402
+
+METRIC = ("zone-burns/sec (FP64, rtol=1e-8) and adjoint gradients/sec vs plain "
+          "GPU launch & CPU oracle")
+WORKLOAD = "chain13_heat"
+WORKLOAD_DESC = ("13-species alpha chain with self-heating (12 rates, Q~U[1,10]), "
+                 "65536 zones, T9 log-U[0.5,5], rho log-U[1e5,1e8], Y0=1/4, "
+                 "t_end 1e-3 s, rtol 1e-8, atol 1e-12")
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2312_02836_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, index: int):
+        self.path = tempfile.mktemp(suffix=".csv")
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={index}", f"--query-gpu={q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        sm, mx, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names[1:], parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def cpu_baseline(name: str, Z_sample: int, zone_offset: int = 0) -> dict:
+    """The oracle, as it stands, on a bounded sample of the workload."""
+    import oracle
+    net, z, s = gen.problem(name, zone_offset + Z_sample)
+    z = {k: v[zone_offset:] for k, v in z.items()}
+    t0 = time.perf_counter()
+    out = oracle.burn(net, z["Y"], z["T9"], z["rho"], s["t_end"], s["rtol"], s["atol"])
+    dt = time.perf_counter() - t0
+    return {"value": Z_sample / dt, "unit": "zone-burns/s", "cores": int(out["threads"]),
+            "kind": "oracle", "seconds": dt,
+            "sample": f"first {Z_sample} zones of {name} (i.i.d. seeded zones), "
+                      f"all host cores"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    Zs = args.ref_zones
+    for _ in range(args.warmup):
+        cpu_baseline(WORKLOAD, max(64, Zs // 16))
+    times = []
+    cores = 0
+    for k in range(args.steps):
+        r = cpu_baseline(WORKLOAD, Zs, zone_offset=k * Zs)
+        times.append(r["seconds"])
+        cores = r["cores"]
+    per = statistics.mean(times)
+    value = Zs / per
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "zone-burns/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC, "zones_per_step": Zs},
+            "cpu_baseline": {"value": value, "unit": "zone-burns/s", "cores": cores,
+                             "kind": "oracle",
+                             "sample": f"{Zs} zones of the workload per step"},
+            "e2e": {"value": value, "unit": "zone-burns/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_native(args):
+    import torch
+    import paper_2312_02836_gb300 as nb
+    from paper_2312_02836_gb300 import metrics
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    Z = args.zones
+    net_spec, zall, s = gen.problem(WORKLOAD, Z * ws)
+    if args.t_end is not None:
+        s["t_end"] = args.t_end
+    z = {k: np.ascontiguousarray(v[rank * Z:(rank + 1) * Z]) for k, v in zall.items()}
+    netc = nb.Network(net_spec)
+    info = netc.info()
+    Y0 = torch.from_numpy(z["Y"]).to(dev)
+    T9 = torch.from_numpy(z["T9"]).to(dev)
+    rho = torch.from_numpy(z["rho"]).to(dev)
+    out = None
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+            torch.cuda.synchronize()
+
+    def step(kernel="persistent"):
+        nonlocal out
+        out = nb.burn(netc, Y0, T9, rho, s["t_end"], s["rtol"], s["atol"],
+                      kernel=kernel, out=out, blocks_per_sm=args.blocks_per_sm,
+                      threads_per_block=args.threads_per_block)
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    clocks = Clocks(torch.cuda.current_device()) if rank == 0 else None
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier()
+    for k in range(args.steps):
+        flush.fill_(float(k))                 # L2 flush, outside the timed events
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    barrier()
+    clk = clocks.stop() if clocks else None
+    ms = [a.elapsed_time(b) for a, b in ev]
+    mean_ms = statistics.mean(ms)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([mean_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        mean_ms = float(t.item())
+    counters = out.counters.cpu().numpy()
+    status = out.status.cpu().numpy()
+    ops = metrics.burn_ops(info, counters, net_spec.self_heating)
+    value = Z * ws / (mean_ms * 1e-3)
+
+    if rank != 0:
+        return
+    # ---- end to end through the host-pointer C entry point (pinned buffers)
+    hY0 = torch.from_numpy(z["Y"]).pin_memory().numpy()
+    hT9 = torch.from_numpy(z["T9"]).pin_memory().numpy()
+    hrho = torch.from_numpy(z["rho"]).pin_memory().numpy()
+    hout = dict(Y=torch.empty((Z, 13), dtype=torch.float64).pin_memory().numpy(),
+                T9=torch.empty(Z, dtype=torch.float64).pin_memory().numpy(),
+                E=torch.empty(Z, dtype=torch.float64).pin_memory().numpy(),
+                counters=torch.empty((Z, 8), dtype=torch.int32).pin_memory().numpy(),
+                status=torch.empty(Z, dtype=torch.int32).pin_memory().numpy())
+    nb.burn_host(netc, hY0, hT9, hrho, s["t_end"], s["rtol"], s["atol"], out=hout)
+    e2e_t = []
+    for _ in range(max(2, min(args.steps, 5))):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        nb.burn_host(netc, hY0, hT9, hrho, s["t_end"], s["rtol"], s["atol"], out=hout)
+        e2e_t.append(time.perf_counter() - t0)
+    assert np.array_equal(hout["Y"], out.Y.cpu().numpy())
+    h2d = hY0.nbytes + hT9.nbytes + hrho.nbytes
+    d2h = sum(a.nbytes for a in hout.values())
+
+    # ---- plain one-thread-per-zone launch, same inputs and tolerances
+    plain_ms = []
+    for k in range(2):
+        flush.fill_(2.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step("plain")
+        b.record(stream)
+        torch.cuda.synchronize()
+        plain_ms.append(a.elapsed_time(b))
+    plain_equal = bool(np.array_equal(out.Y.cpu().numpy(), hout["Y"]))
+
+    # ---- roofline of the burn kernel (one launch per step)
+    achieved = ops["flops"] / (mean_ms * 1e-3) / 1e12
+    peak = metrics.FP64_PEAK_TFLOPS
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "burn_traffic.json")
+    if os.path.exists(tpath):
+        tj = json.load(open(tpath))
+        if tj.get("source_hash") == kernel_source_hash() and tj.get("zones") == Z:
+            traffic = tj.get("dram_bytes_per_launch")
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": "k_burn_persistent",
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2070 MHz",
+                "flops_per_launch": ops["flops"],
+                "special_functions_per_launch": ops["special"],
+                "algorithmic_bytes_per_launch": int(Z * (13 * 8 * 2 + 8 * 4 + 8 * 4 + 4))}
+
+    base = None
+    if not args.no_cpu_baseline:
+        base = cpu_baseline(WORKLOAD, args.cpu_zones)
+        base.pop("seconds", None)
+
+    adj = None
+    if args.adjoint:
+        adj = adjoint_bench(nb, torch, dev, flush, metrics)
+
+    line = {"metric": METRIC, "value": value, "unit": "zone-burns/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC, "zones_per_gpu": Z,
+                       "l2": "256 MiB buffer written between timed steps (L2 flush)",
+                       "kernel": "persistent lane-per-zone, device work queue"},
+            "roofline": roofline, "cpu_baseline": base,
+            "e2e": {"value": Z / statistics.mean(e2e_t), "unit": "zone-burns/s",
+                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                    "path": "nb_burn_batch_host (pinned host buffers, copies inside)"},
+            "gpu_launches": args.steps,
+            "clocks": clk,
+            "plain_launch": {"value": Z / (statistics.mean(plain_ms) * 1e-3),
+                             "unit": "zone-burns/s", "ms": statistics.mean(plain_ms),
+                             "bitwise_equal_to_persistent": plain_equal},
+            "zones_ok": int((status == 0).sum()),
+            "events": ops["events"]}
+    if adj is not None:
+        line["adjoint"] = adj
+    print(json.dumps(line), flush=True)
+
+
+def adjoint_bench(nb, torch, dev, flush, metrics) -> dict:
+    """Adjoint gradients/s: the 48-species sensitivity workload, 6 cotangents
+    per zone (energy + the 5 largest final abundances), forward with tape
+    plus reverse sweep."""
+    name = "net48_adjoint"
+    net, z, s = gen.problem(name)
+    Z = z["T9"].shape[0]
+    nc = nb.Network(net)
+    info = nc.info()
+    Y0 = torch.from_numpy(z["Y"]).to(dev)
+    T9 = torch.from_numpy(z["T9"]).to(dev)
+    rho = torch.from_numpy(z["rho"]).to(dev)
+    tape = nb.Tape(nc, Z, 4000)
+    fw = nb.burn(nc, Y0, T9, rho, s["t_end"], s["rtol"], s["atol"], tape=tape)
+    torch.cuda.synchronize()
+    Yf = fw.Y.cpu().numpy()
+    top = gen.largest_species(Yf, 5)
+    K = 6
+    gY = np.zeros((K, Z, net.N))
+    gE = np.zeros((K, Z))
+    gE[0] = 1.0
+    for q in range(5):
+        gY[q + 1, np.arange(Z), top[:, q]] = 1.0
+    gYd = torch.from_numpy(gY).to(dev)
+    gEd = torch.from_numpy(gE).to(dev)
+    nb.adjoint(nc, tape, gYd, gEd)
+    torch.cuda.synchronize()
+    flush.fill_(3.0)
+    a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    a.record()
+    fw = nb.burn(nc, Y0, T9, rho, s["t_end"], s["rtol"], s["atol"], tape=tape)
+    b.record()
+    nb.adjoint(nc, tape, gYd, gEd)
+    c.record()
+    torch.cuda.synchronize()
+    fwd_ms, adj_ms = a.elapsed_time(b), b.elapsed_time(c)
+    st = fw.status.cpu().numpy()
+    steps = int(fw.counters.cpu().numpy()[:, 0].sum())
+    flops = metrics.adjoint_ops(info, steps, K, net.self_heating)
+    return {"workload": "48 species / 180 rates, 16384 zones, T9 log-U[0.3,6], "
+                        "rho log-U[1e4,1e9], t_end 1e-2, 6 cotangents per zone",
+            "value": Z * K / ((fwd_ms + adj_ms) * 1e-3), "unit": "gradients/s",
+            "gradient_length": net.R, "forward_ms": fwd_ms, "reverse_ms": adj_ms,
+            "zones_ok": int((st == 0).sum()),
+            "reverse_tflops": flops / (adj_ms * 1e-3) / 1e12}
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["native", "reference"], default="native")
+    p.add_argument("--zones", type=int, default=gen.CONFIGS[WORKLOAD]["Z"])
+    p.add_argument("--t-end", type=float, default=None,
+                   help="override t_end (profiling of a shorter burn only)")
+    p.add_argument("--blocks-per-sm", type=int, default=0)
+    p.add_argument("--threads-per-block", type=int, default=0)
+    p.add_argument("--cpu-zones", type=int, default=8192)
+    p.add_argument("--ref-zones", type=int, default=4096)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--adjoint", action=argparse.BooleanOptionalAction, default=True)
+    args = p.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,186 @@
+/*
+ * netburn.h -- C ABI of the GB300 batched reaction-network burner.
+ *
+ * The operation: arXiv:2312.02836 (Chen, Johnson, Katz, Smith Clark, Boyd,
+ * Zingale, "A Framework for Exploring Nuclear Physics Sensitivity in
+ * Numerical Simulations") generates a reaction network's right-hand side and
+ * analytic Jacobian (Sec. 2) and integrates it per zone with a stiff
+ * implicit integrator, optionally with self-heating (Sec. 2, Microphysics;
+ * Sec. 3, every zone of the Castro detonation).  This library does that
+ * per-zone burn for many zones at once on one GPU, and the sensitivity of
+ * the result to every rate (the quantity the paper's Sec. 1 and Sec. 3 study
+ * by re-running with changed networks).
+ *
+ * Model per zone (state x = [Y_0..Y_{N-1}] plus T9 when self-heating):
+ *   lambda_r(T9) = exp(a0 + a1/T9 + a2 T9^(-1/3) + a3 T9^(1/3) + a4 T9
+ *                      + a5 T9^(5/3) + a6 ln T9)      (ReacLib fit, Sec. 2)
+ *   R_r   = scale_r exp(p_r) rho^(n_r-1) lambda_r(T9) prod_j Y_j
+ *   dY_i/dt = sum_r c_ir R_r,   c_ir = #i in products - #i in reactants
+ *   edot  = sum_r Q_r R_r,  dE/dt = edot,  dT9/dt = edot / c_v,
+ *   c_v   = 1.5 sum_i Y_i + 1e-3 T9^3
+ * Integrator: variable-step, variable-order (1..5) BDF in Lagrange form with
+ * a modified Newton iteration (the VODE family named in Sec. 2), with the
+ * step, order and Newton rules listed in this project's design notes.
+ *
+ * Conventions for every entry point:
+ *  - Return value: NB_OK (0) or a negative NB_E* code; nb_strerror() names it.
+ *    Argument checks happen before any GPU work; on error nothing is written.
+ *  - Device pointers are owned by the caller and must stay valid until the
+ *    work queued on `stream` has finished.  Work is asynchronous on `stream`
+ *    (a cudaStream_t passed as void*; NULL = the legacy default stream)
+ *    unless the function says otherwise.
+ *  - Arrays are dense, row-major, FP64 unless stated: [Z, N] means zone-major.
+ *  - Per-zone outcomes are in status[] (NB_Z_*), never an error code.
+ *  - An nb_net is not safe for concurrent burns from several host threads:
+ *    its device workspace is shared.
+ */
+#ifndef NETBURN_H
+#define NETBURN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* call-level error codes */
+#define NB_OK 0
+#define NB_E_ARG -1          /* bad argument (null pointer, size, tolerance) */
+#define NB_E_TOPOLOGY -2     /* species index out of range, empty reaction */
+#define NB_E_TOO_LARGE -3    /* network exceeds the compiled limits */
+#define NB_E_CUDA -4         /* a CUDA runtime call failed */
+#define NB_E_NOMEM -5        /* host or device allocation failed */
+#define NB_E_TAPE -6         /* tape missing, too small or from another net */
+
+/* per-zone status */
+#define NB_Z_OK 0
+#define NB_Z_MAX_STEPS 1     /* more than max_attempts step attempts */
+#define NB_Z_DT_UNDERFLOW 2  /* step below 1e-30 t_end or 1e-14 t */
+#define NB_Z_NEWTON_FAIL 3   /* 10 consecutive Newton failures */
+#define NB_Z_TAPE_FULL 4     /* adjoint tape capacity exceeded */
+#define NB_Z_NONFINITE 5     /* non-finite input, rate or first derivative */
+
+/* per-zone counters, counters[z * NB_NCOUNT + c] */
+#define NB_NCOUNT 8
+#define NB_C_ACCEPTED 0
+#define NB_C_REJ_ERROR 1
+#define NB_C_REJ_NEWTON 2
+#define NB_C_NEWTON_ITERS 3
+#define NB_C_JACOBIANS 4     /* = LU factorizations */
+#define NB_C_RHS 5
+#define NB_C_RATE_EVALS 6    /* evaluations of all lambda_r(T9) */
+#define NB_C_EDOT 7          /* energy-only evaluations for E */
+
+typedef struct nb_net_s* nb_net;
+
+/* Network topology (host pointers, copied by nb_net_load). */
+typedef struct {
+  int32_t n_species;        /* N >= 1 */
+  int32_t n_reactions;      /* R >= 0 */
+  const int16_t* reactants; /* [R, 3] species indices, -1 padded; >= 1 each */
+  const int16_t* products;  /* [R, 3] species indices, -1 padded */
+  const double* Q;          /* [R] energy per reaction, or NULL (no E) */
+  const double* scale;      /* [R] constant factor scale_r, or NULL (= 1) */
+  int32_t self_heating;     /* 1: T9 is integrated (requires Q) */
+} nb_topology;
+
+typedef struct {
+  int32_t n_state;          /* N + self_heating */
+  int32_t n_reactions;
+  int32_t nnz_jacobian;     /* structural nonzeros of alpha0 I - h J */
+  int32_t nnz_lu;           /* after the fill of the pre-ordered LU */
+  int32_t n_dterms;         /* distinct (reaction, reactant) derivatives */
+  int32_t lane_doubles;     /* device workspace per zone in flight */
+  int32_t blob_bytes;       /* compiled network size (shared memory) */
+  int32_t has_energy;
+  /* algorithmic FP64 operations per event, an FMA counted as 2; exp, log,
+   * cbrt, pow, sqrt and divisions are special functions, not flops */
+  int64_t flops_rate_eval;  /* all k_r at one T9 (NB_C_RATE_EVALS) */
+  int64_t flops_rate_deriv; /* extra for d ln lambda_r/dT9 (self-heating Jacobian) */
+  int64_t flops_terms;      /* R_r = k_r prod Y (per RHS and per E evaluation) */
+  int64_t flops_rhs;        /* f from R_r (NB_C_RHS) */
+  int64_t flops_jacobian;   /* derivative terms + assembly of M (NB_C_JACOBIANS) */
+  int64_t flops_lu;         /* static-pivot factorisation (NB_C_JACOBIANS) */
+  int64_t flops_solve;      /* forward + back substitution (NB_C_NEWTON_ITERS) */
+  int64_t flops_edot;       /* edot from R_r (NB_C_EDOT) */
+  int64_t flops_tsolve;     /* transposed solves of the adjoint, per cotangent */
+  int32_t exp_per_rate_eval;
+  int32_t reserved;
+} nb_net_info;
+
+typedef struct {
+  int32_t max_attempts;     /* step attempts per zone (default 500000) */
+  int32_t kernel;           /* NB_KERNEL_* */
+  int32_t threads_per_block;/* 0 = library choice */
+  int32_t blocks_per_sm;    /* 0 = library choice (persistent kernel) */
+  int32_t blob_in_shared;   /* -1 auto, 0 global (L1), 1 shared memory */
+  int32_t reserved[3];
+} nb_options;
+
+#define NB_KERNEL_PERSISTENT 0  /* lane-per-zone, device work queue */
+#define NB_KERNEL_PLAIN 1       /* one thread per zone, no queue */
+
+/* Compile a network: validate the topology, build the Jacobian sparsity
+ * pattern, choose a minimum-degree elimination order, compute the LU fill
+ * and the gather programs, and upload them to the current device.
+ * coeffs: [R, 7] host array of (a0..a6).  *out receives a handle to free
+ * with nb_net_free.  Synchronous. */
+int nb_net_load(const nb_topology* topo, const double* coeffs, nb_net* out);
+int nb_net_free(nb_net net);
+int nb_net_get_info(nb_net net, nb_net_info* out);
+
+/* Fill *opt with the defaults. */
+void nb_default_options(nb_options* opt);
+
+/* Burn Z zones from t = 0 to t_end.
+ *  Y0 [Z, N], T9_0 [Z], rho [Z]       device inputs
+ *  ln_mult   NULL, [R] (per_zone = 0) or [Z, R] (per_zone = 1): p_r above
+ *  Y [Z, N], T9 [Z]                   device outputs (may alias Y0, T9_0)
+ *  E [Z]                              device output or NULL (0 without Q)
+ *  counters [Z, NB_NCOUNT] int32, status [Z] int32  device outputs
+ *  rtol > 0, atol > 0, t_end >= 0.  opt may be NULL (defaults).
+ *  tape: NULL, or a tape from nb_tape_alloc to record the accepted
+ *  schedule for nb_burn_adjoint.  Z = 0 is a no-op. */
+int nb_burn_batch(nb_net net, int64_t Z, const double* Y0, const double* T9_0,
+                  const double* rho, double t_end, double rtol, double atol,
+                  const double* ln_mult, int32_t ln_mult_per_zone, double* Y,
+                  double* T9, double* E, int32_t* counters, int32_t* status,
+                  const nb_options* opt, void* tape, void* stream);
+
+/* Same burn from HOST arrays (pageable or pinned): copies the inputs to
+ * library-owned device buffers, burns, copies the outputs back and waits
+ * for the stream.  Synchronous.  E, counters may be NULL. */
+int nb_burn_batch_host(nb_net net, int64_t Z, const double* Y0,
+                       const double* T9_0, const double* rho, double t_end,
+                       double rtol, double atol, const double* ln_mult,
+                       int32_t ln_mult_per_zone, double* Y, double* T9,
+                       double* E, int32_t* counters, int32_t* status,
+                       const nb_options* opt, void* stream);
+
+/* Adjoint tape: per zone up to max_steps accepted steps (time, order,
+ * state, energy) in device memory owned by the tape.  Synchronous. */
+int nb_tape_alloc(nb_net net, int64_t Z, int32_t max_steps, void** tape);
+int nb_tape_free(void* tape);
+/* Device pointer to the accepted-step counts [Z] int32 of the last burn
+ * recorded on the tape. */
+int nb_tape_steps(void* tape, const int32_t** steps);
+
+/* Discrete adjoint of a recorded burn (same net, same ln_mult, same
+ * inputs).  K cotangent sets per zone:
+ *  gY [K, Z, N], gE [K, Z] or NULL, gT9 [K, Z] or NULL   device inputs
+ *  d_ln_mult [K, Z, R]   device output: d(sum of cotangent . outputs)/dp_r
+ *  dY0 [K, Z, N] or NULL, dT0 [K, Z] or NULL  device outputs
+ * The schedule (step times and orders) is held fixed and the Newton
+ * solutions are treated as exact: this is the exact gradient of the
+ * discrete map the forward burn computed.  Zones whose forward status was
+ * not NB_Z_OK get zero gradients. */
+int nb_burn_adjoint(nb_net net, void* tape, int32_t K, const double* gY,
+                    const double* gE, const double* gT9, double* d_ln_mult,
+                    double* dY0, double* dT0, void* stream);
+
+const char* nb_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NETBURN_H */

@@ -1,0 +1,327 @@
+"""GB300 batched stiff reaction-network burner (arXiv:2312.02836).
+
+Python binding of the C ABI in ``include/netburn.h``.  PyTorch supplies the
+device memory and the stream; every step of the burn runs in the CUDA
+library (``_build/libnetburn.so``).  There is no CPU path: without a CUDA
+device the calls raise.
+
+    net = Network(spec)                       # compile a network
+    out = burn(net, Y0, T9, rho, t_end, rtol, atol)   # torch CUDA float64
+    Y, T9, E = Burn.apply(Y0, T9, rho, ln_mult, net, t_end, rtol, atol)
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import NamedTuple, Optional
+
+import numpy as np
+
+from . import _abi
+from ._abi import (COUNTER_NAMES, KERNEL_PERSISTENT, KERNEL_PLAIN, NCOUNT,
+                   ZONE_STATUS, NetburnError)
+
+__all__ = ["Network", "burn", "burn_host", "Tape", "adjoint", "Burn",
+           "BurnResult", "NetburnError", "COUNTER_NAMES", "ZONE_STATUS",
+           "KERNEL_PERSISTENT", "KERNEL_PLAIN", "library_path"]
+
+
+def library_path() -> str:
+    from . import build
+    return build.LIB
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise NetburnError("no CUDA device: the burn runs only on the GPU")
+    return torch
+
+
+def _np(a, dtype):
+    return None if a is None else np.ascontiguousarray(a, dtype=dtype)
+
+
+class Network:
+    """A compiled network on the current CUDA device.
+
+    ``spec`` has attributes N, R, reactants [R,3], products [R,3] (int,
+    -1 padded), coeffs [R,7], Q [R] or None, scale [R] or None and
+    self_heating."""
+
+    def __init__(self, spec):
+        _torch()
+        lib = _abi.load()
+        self.N = int(spec.N)
+        self.R = int(spec.R)
+        self.self_heating = bool(spec.self_heating)
+        self._reac = _np(spec.reactants, np.int16)
+        self._prod = _np(spec.products, np.int16)
+        self._coef = _np(spec.coeffs, np.float64)
+        self._Q = _np(getattr(spec, "Q", None), np.float64)
+        self._scale = _np(getattr(spec, "scale", None), np.float64)
+        self.has_energy = self._Q is not None
+        p = lambda a: None if a is None else a.ctypes.data
+        topo = _abi.Topology(self.N, self.R, p(self._reac), p(self._prod),
+                             p(self._Q), p(self._scale), int(self.self_heating))
+        h = C.c_void_p()
+        _abi.check(lib.nb_net_load(C.byref(topo), p(self._coef), C.byref(h)),
+                   "nb_net_load")
+        self._h = h
+        self.n = self.N + (1 if self.self_heating else 0)
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise NetburnError("network was freed")
+        return self._h
+
+    def info(self) -> dict:
+        lib = _abi.load()
+        out = _abi.NetInfo()
+        _abi.check(lib.nb_net_get_info(self.handle, C.byref(out)), "nb_net_get_info")
+        return {name: getattr(out, name) for name, _ in out._fields_
+                if name != "reserved"}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            _abi.load().nb_net_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BurnResult(NamedTuple):
+    Y: "object"
+    T9: "object"
+    E: "object"
+    counters: "object"
+    status: "object"
+
+
+def _options(kernel, threads_per_block, blocks_per_sm, blob_in_shared,
+             max_attempts):
+    o = _abi.Options()
+    _abi.load().nb_default_options(C.byref(o))
+    if isinstance(kernel, str):
+        kernel = {"persistent": KERNEL_PERSISTENT, "plain": KERNEL_PLAIN}[kernel]
+    o.kernel = int(kernel)
+    o.threads_per_block = int(threads_per_block)
+    o.blocks_per_sm = int(blocks_per_sm)
+    o.blob_in_shared = int(blob_in_shared)
+    o.max_attempts = int(max_attempts)
+    return o
+
+
+def _dev(t, torch, name, shape=None):
+    if t is None:
+        return None
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64):
+        raise NetburnError(f"{name} must be a CUDA float64 tensor")
+    if not t.is_contiguous():
+        raise NetburnError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise NetburnError(f"{name} has shape {tuple(t.shape)}, expected {shape}")
+    return t
+
+
+def burn(net: Network, Y0, T9, rho, t_end: float, rtol: float, atol: float,
+         ln_mult=None, *, kernel="persistent", tape: "Optional[Tape]" = None,
+         threads_per_block=0, blocks_per_sm=0, blob_in_shared=-1,
+         max_attempts=500000, stream=None, out: Optional[BurnResult] = None):
+    """Burn Z zones on the GPU.  Y0 [Z,N], T9 [Z], rho [Z] CUDA float64;
+    ln_mult None, [R] or [Z,R].  Returns BurnResult of CUDA tensors."""
+    torch = _torch()
+    Z = int(Y0.shape[0]) if Y0.dim() == 2 else 0
+    _dev(Y0, torch, "Y0", (Z, net.N))
+    _dev(T9, torch, "T9", (Z,))
+    _dev(rho, torch, "rho", (Z,))
+    per_zone = 0
+    if ln_mult is not None:
+        _dev(ln_mult, torch, "ln_mult")
+        if ln_mult.dim() == 2:
+            per_zone = 1
+            if tuple(ln_mult.shape) != (Z, net.R):
+                raise NetburnError("ln_mult must be [R] or [Z, R]")
+        elif tuple(ln_mult.shape) != (net.R,):
+            raise NetburnError("ln_mult must be [R] or [Z, R]")
+    dev = Y0.device
+    if out is None:
+        out = BurnResult(torch.empty((Z, net.N), dtype=torch.float64, device=dev),
+                         torch.empty((Z,), dtype=torch.float64, device=dev),
+                         torch.empty((Z,), dtype=torch.float64, device=dev),
+                         torch.empty((Z, NCOUNT), dtype=torch.int32, device=dev),
+                         torch.empty((Z,), dtype=torch.int32, device=dev))
+    o = _options(kernel, threads_per_block, blocks_per_sm, blob_in_shared,
+                 max_attempts)
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    lib = _abi.load()
+    ptr = lambda t: None if t is None else t.data_ptr()
+    rc = lib.nb_burn_batch(net.handle, Z, ptr(Y0), ptr(T9), ptr(rho),
+                           float(t_end), float(rtol), float(atol), ptr(ln_mult),
+                           per_zone, ptr(out.Y), ptr(out.T9), ptr(out.E),
+                           ptr(out.counters), ptr(out.status), C.byref(o),
+                           None if tape is None else tape.handle,
+                           C.c_void_p(st.cuda_stream))
+    _abi.check(rc, "nb_burn_batch")
+    if tape is not None:
+        tape._recorded(Z, ln_mult, float(t_end), float(rtol), float(atol))
+    return out
+
+
+def burn_host(net: Network, Y0, T9, rho, t_end, rtol, atol, ln_mult=None, *,
+              kernel="persistent", threads_per_block=0, blocks_per_sm=0,
+              blob_in_shared=-1, max_attempts=500000, stream=None, out=None):
+    """Burn from host (numpy) arrays through ``nb_burn_batch_host``: the
+    library copies the inputs in, burns and copies the outputs back.
+    Returns a dict of numpy arrays; ``out`` may supply preallocated (e.g.
+    pinned) output arrays."""
+    torch = _torch()
+    Y0 = _np(Y0, np.float64)
+    Z = Y0.shape[0]
+    T9 = _np(T9, np.float64)
+    rho = _np(rho, np.float64)
+    lm = _np(ln_mult, np.float64)
+    per_zone = 1 if (lm is not None and lm.ndim == 2) else 0
+    if out is None:
+        out = dict(Y=np.empty((Z, net.N)), T9=np.empty(Z), E=np.empty(Z),
+                   counters=np.empty((Z, NCOUNT), np.int32),
+                   status=np.empty(Z, np.int32))
+    o = _options(kernel, threads_per_block, blocks_per_sm, blob_in_shared,
+                 max_attempts)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    p = lambda a: None if a is None else a.ctypes.data
+    rc = _abi.load().nb_burn_batch_host(
+        net.handle, Z, p(Y0), p(T9), p(rho), float(t_end), float(rtol),
+        float(atol), p(lm), per_zone, p(out["Y"]), p(out["T9"]), p(out["E"]),
+        p(out["counters"]), p(out["status"]), C.byref(o),
+        C.c_void_p(st.cuda_stream))
+    _abi.check(rc, "nb_burn_batch_host")
+    return out
+
+
+class Tape:
+    """Device record of a burn's accepted steps, for ``adjoint``."""
+
+    def __init__(self, net: Network, Z: int, max_steps: int):
+        _torch()
+        self.net = net
+        self.Z = int(Z)
+        self.max_steps = int(max_steps)
+        h = C.c_void_p()
+        _abi.check(_abi.load().nb_tape_alloc(net.handle, self.Z, self.max_steps,
+                                             C.byref(h)), "nb_tape_alloc")
+        self._h = h
+        self.recorded = None
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise NetburnError("tape was freed")
+        return self._h
+
+    def _recorded(self, Z, ln_mult, t_end, rtol, atol):
+        self.recorded = dict(Z=Z, per_zone=(ln_mult is not None and ln_mult.dim() == 2),
+                             t_end=t_end, rtol=rtol, atol=atol)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            _abi.load().nb_tape_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def adjoint(net: Network, tape: Tape, gY, gE=None, gT9=None, *, stream=None,
+            want_initial=True):
+    """Discrete adjoint of the burn recorded on ``tape``.  gY [K,Z,N], gE and
+    gT9 [K,Z] (or None).  Returns (d_ln_mult [K,Z,R], dY0 [K,Z,N], dT0 [K,Z])."""
+    torch = _torch()
+    if tape.recorded is None:
+        raise NetburnError("tape holds no burn")
+    Z = tape.recorded["Z"]
+    if gY.dim() == 2:
+        gY = gY.unsqueeze(0)
+    K = int(gY.shape[0])
+    _dev(gY, torch, "gY", (K, Z, net.N))
+    if gE is not None:
+        gE = gE.reshape(K, Z).contiguous()
+        _dev(gE, torch, "gE", (K, Z))
+    if gT9 is not None:
+        gT9 = gT9.reshape(K, Z).contiguous()
+        _dev(gT9, torch, "gT9", (K, Z))
+    dev = gY.device
+    dl = torch.empty((K, Z, net.R), dtype=torch.float64, device=dev)
+    dY0 = torch.empty((K, Z, net.N), dtype=torch.float64, device=dev) if want_initial else None
+    dT0 = torch.empty((K, Z), dtype=torch.float64, device=dev) if want_initial else None
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    ptr = lambda t: None if t is None else t.data_ptr()
+    rc = _abi.load().nb_burn_adjoint(net.handle, tape.handle, K, ptr(gY), ptr(gE),
+                                     ptr(gT9), ptr(dl), ptr(dY0), ptr(dT0),
+                                     C.c_void_p(st.cuda_stream))
+    _abi.check(rc, "nb_burn_adjoint")
+    return dl, dY0, dT0
+
+
+def _autograd():
+    import torch
+
+    class Burn(torch.autograd.Function):
+        """(Y0, T9, rho, ln_mult) -> (Y, T9, E) with a discrete-adjoint
+        backward.  ln_mult may be [R] (shared) or [Z, R]; its gradient is
+        d/d ln(rate multiplier) of every reaction."""
+
+        @staticmethod
+        def forward(ctx, Y0, T9, rho, ln_mult, net, t_end, rtol, atol,
+                    max_steps=20000):
+            Z = Y0.shape[0]
+            lm = None
+            if ln_mult is not None:
+                lm = ln_mult.detach().contiguous()
+            tape = Tape(net, Z, max_steps)
+            out = burn(net, Y0.detach().contiguous(), T9.detach().contiguous(),
+                       rho.detach().contiguous(), t_end, rtol, atol, lm, tape=tape)
+            ctx.tape = tape
+            ctx.net = net
+            ctx.shared = ln_mult is not None and ln_mult.dim() == 1
+            ctx.has_mult = ln_mult is not None
+            ctx.mark_non_differentiable(out.counters, out.status)
+            return out.Y, out.T9, out.E, out.counters, out.status
+
+        @staticmethod
+        def backward(ctx, gY, gT9, gE, _gc, _gs):
+            net = ctx.net
+            torch_ = torch
+            Z = gY.shape[0] if gY is not None else ctx.tape.recorded["Z"]
+            dev = gY.device if gY is not None else gT9.device
+            if gY is None:
+                gY = torch_.zeros((Z, net.N), dtype=torch_.float64, device=dev)
+            dl, dY0, dT0 = adjoint(net, ctx.tape, gY.contiguous().unsqueeze(0),
+                                   None if gE is None else gE.contiguous().unsqueeze(0),
+                                   None if gT9 is None else gT9.contiguous().unsqueeze(0))
+            dl, dY0, dT0 = dl[0], dY0[0], dT0[0]
+            g_lm = None
+            if ctx.has_mult:
+                g_lm = dl.sum(0) if ctx.shared else dl
+            return dY0, dT0, None, g_lm, None, None, None, None, None
+
+    return Burn
+
+
+class _LazyBurn:
+    _cls = None
+
+    def __getattr__(self, name):
+        if _LazyBurn._cls is None:
+            _LazyBurn._cls = _autograd()
+        return getattr(_LazyBurn._cls, name)
+
+
+Burn = _LazyBurn()

@@ -1,0 +1,305 @@
+// adjoint.cu -- discrete adjoint of a recorded burn.
+//
+// The rate sensitivity the paper explores by re-running the detonation with
+// changed networks (arXiv:2312.02836 Sec. 1 and Sec. 3) is computed here as
+// the exact gradient of the discrete map the forward burn applied, with the
+// step schedule (t_n, h_n, k_n) frozen and every Newton solution treated as
+// exact.  Forward step s solves
+//     G_s = alpha_0 x_s + sum_{j=1..k} alpha_j x_{s-j} - h f(x_s; p) = 0,
+//     E_s = (h edot(x_s; p) - sum_j alpha_j E_{s-j}) / alpha_0,
+// so, walking s = S..1 with cotangents lam_s (of x_s) and e_s (of E_s):
+//     lam_s += e_s h / alpha_0 * d edot / dx,   e_{s-j} -= e_s alpha_j / alpha_0
+//     (alpha_0 I - h J(x_s))^T mu = lam_s
+//     lam_{s-j} -= alpha_j mu
+//     dL/dp_r += R_r(x_s) (h c_r^T mu + e_s h / alpha_0 Q_r)
+// (plus mu_T Q_r / c_v in c_r^T mu under self-heating, and the temperature
+// derivative through g_r = d ln lambda_r / dT9 when T9 is a parameter).
+// One lane per zone, K cotangent sets share each LU factorisation.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "blob.h"
+#include "device.cuh"
+#include "host.h"
+#include "../../include/netburn.h"
+
+using namespace nb;
+
+namespace {
+
+struct AdjParams {
+  const unsigned char* blob;
+  int blob_bytes, blob_in_smem;
+  long long Z;
+  int K;
+  TapeDev tape;
+  const double* lnm;
+  int lnm_per_zone;
+  const double *gY, *gE, *gT9;
+  double *dl, *dY0, *dT0;
+  double* ws;
+  long long lane_doubles;  // adjoint workspace per lane
+  int o_lam, o_ee, o_gr, o_gt, o_mu, o_de;
+  unsigned long long* queue;
+};
+
+struct AdjZone {
+  long long z;
+  int s;        // next step to reverse
+  bool sh_dummy;
+  Zone fz;      // rates context (rho, lnm)
+};
+
+__device__ __forceinline__ int ring(int s) { return s % HMAX; }
+
+__device__ __forceinline__ const double* rec_ptr(const Net& t, const AdjParams& A,
+                                                 long long z, int s) {
+  return A.tape.rec + ((size_t)z * A.tape.cap + s) * (t.n + 3);
+}
+
+struct AWS {
+  LV lam, ee, gr, gt, mu, de;
+};
+
+__device__ __forceinline__ AWS make_aws(const AdjParams& A, double* lane_base) {
+  AWS a;
+  a.lam.p = lane_base + (size_t)A.o_lam * WS_LANES;
+  a.ee.p = lane_base + (size_t)A.o_ee * WS_LANES;
+  a.gr.p = lane_base + (size_t)A.o_gr * WS_LANES;
+  a.gt.p = lane_base + (size_t)A.o_gt * WS_LANES;
+  a.mu.p = lane_base + (size_t)A.o_mu * WS_LANES;
+  a.de.p = lane_base + (size_t)A.o_de * WS_LANES;
+  return a;
+}
+
+// returns true when the zone needs no reverse steps
+__device__ bool adj_init(const Net& t, AdjZone& Zs, const WS& w, const AWS& a,
+                         const AdjParams& A) {
+  const long long z = Zs.z;
+  const int n = t.n, N = t.N, K = A.K;
+  const int st = A.tape.zstat[z];
+  const int S = A.tape.steps[z] - 1;
+  for (int e = 0; e < HMAX * K * n; ++e) a.lam[e] = 0.0;
+  for (int e = 0; e < HMAX * K; ++e) a.ee[e] = 0.0;
+  for (int e = 0; e < K * t.R; ++e) a.gr[e] = 0.0;
+  for (int q = 0; q < K; ++q) a.gt[q] = 0.0;
+  Zs.s = (st == NB_Z_OK && S >= 0) ? S : -1;
+  if (Zs.s < 0) return true;
+  const int sl = ring(S);
+  for (int q = 0; q < K; ++q) {
+    const size_t qz = (size_t)q * A.Z + z;
+    for (int i = 0; i < N; ++i) a.lam[(sl * K + q) * n + i] = A.gY[qz * N + i];
+    if (t.sh) a.lam[(sl * K + q) * n + N] = A.gT9 ? A.gT9[qz] : 0.0;
+    a.ee[sl * K + q] = A.gE ? A.gE[qz] : 0.0;
+  }
+  Zone& s = Zs.fz;
+  s.z = z;
+  s.rho = A.tape.rho[z];
+  s.rho2 = s.rho * s.rho;
+  s.T9f = A.tape.T9f[z];
+  s.lnm = A.lnm ? (A.lnm_per_zone ? A.lnm + (size_t)z * t.R : A.lnm) : nullptr;
+  if (!t.sh) eval_rates(t, s, w, s.T9f, true);
+  return S == 0;
+}
+
+// reverse one step; returns true when the zone is done
+__device__ bool adj_step(const Net& t, AdjZone& Zs, const WS& w, const AWS& a,
+                         const AdjParams& A) {
+  const long long z = Zs.z;
+  const int n = t.n, N = t.N, K = A.K, s = Zs.s;
+  const double* rs = rec_ptr(t, A, z, s);
+  const int kk = A.tape.ord[(size_t)z * A.tape.cap + s];
+  const double h = rs[1];
+  double tau[KMAX + 1];
+  tau[0] = rs[0];
+#pragma unroll
+  for (int j = 1; j <= KMAX; ++j) tau[j] = (j <= kk) ? rec_ptr(t, A, z, s - j)[0] : 0.0;
+  double alpha[KMAX + 1];
+  bdf_alpha(kk, tau, h, alpha);
+  for (int i = 0; i < n; ++i) w.x[i] = rs[2 + i];
+  if (t.sh) eval_rates(t, Zs.fz, w, w.x[N], true);
+  eval_terms(t, w, w.x);
+  assemble_M(t, w, w.x, alpha[0], h);
+  factor_M(t, w);
+  double icv = 0.0;
+  if (t.sh) icv = 1.0 / heat_capacity(t, w.x);
+  if (t.hasE) {
+    for (int i = 0; i < n; ++i) a.de[i] = 0.0;
+    for (int d = 0; d < t.nd; ++d) a.de[t.dt_j[d]] += t.Q[t.dt_r[d]] * w.dt[d];
+    if (t.sh) {
+      double acc = 0.0;
+      for (int r = 0; r < t.R; ++r) acc = fma(t.Q[r], w.dt[t.nd + r], acc);
+      a.de[N] = acc;
+    }
+  }
+  const double ia0 = 1.0 / alpha[0];
+  const int sl = ring(s);
+  int sj[KMAX + 1];
+#pragma unroll
+  for (int j = 1; j <= KMAX; ++j) sj[j] = ring(s + HMAX - j);
+  for (int q = 0; q < K; ++q) {
+    const int lo = (sl * K + q) * n;
+    const double es = a.ee[sl * K + q];
+    const double ce = es * h * ia0;
+    for (int i = 0; i < n; ++i) {
+      double v = a.lam[lo + i];
+      if (t.hasE) v = fma(ce, a.de[i], v);
+      a.mu[i] = v;
+      a.lam[lo + i] = 0.0;
+    }
+    a.ee[sl * K + q] = 0.0;
+    tri_solve(t.tfw, t.tfw_s, t.tfw_c, n, w.lu, a.mu);
+    tri_solve(t.tbw, t.tbw_s, t.tbw_c, n, w.lu, a.mu);
+#pragma unroll
+    for (int j = 1; j <= KMAX; ++j) {
+      if (j > kk) continue;
+      const int lj = (sj[j] * K + q) * n;
+      const double ma = -alpha[j];
+      for (int i = 0; i < n; ++i) a.lam[lj + i] = fma(ma, a.mu[i], a.lam[lj + i]);
+      if (t.hasE) a.ee[sj[j] * K + q] = fma(-es * ia0, alpha[j], a.ee[sj[j] * K + q]);
+    }
+    const double muT = t.sh ? a.mu[N] * icv : 0.0;
+    double gt = 0.0;
+    for (int r = 0; r < t.R; ++r) {
+      double acc = 0.0;
+      for (int e = t.rg_ptr[r]; e < t.rg_ptr[r + 1]; ++e)
+        acc = fma(t.rg_c[e], a.mu[t.rg_i[e]], acc);
+      const double Qr = t.Q[r];
+      acc = fma(muT, Qr, acc);
+      const double v = w.rr[r] * fma(h, acc, ce * Qr);
+      a.gr[q * t.R + r] += v;
+      if (!t.sh) gt = fma(v, w.g[r], gt);
+    }
+    a.gt[q] += gt;
+  }
+  Zs.s = s - 1;
+  return Zs.s == 0;
+}
+
+__device__ void adj_finish(const Net& t, const AdjZone& Zs, const AWS& a,
+                           const AdjParams& A) {
+  const long long z = Zs.z;
+  const int n = t.n, N = t.N, K = A.K;
+  const bool ok = Zs.s == 0;
+  const int s0 = ring(0);
+  for (int q = 0; q < K; ++q) {
+    const size_t qz = (size_t)q * A.Z + z;
+    for (int r = 0; r < t.R; ++r) A.dl[qz * t.R + r] = ok ? a.gr[q * t.R + r] : 0.0;
+    if (A.dY0)
+      for (int i = 0; i < N; ++i) A.dY0[qz * N + i] = ok ? a.lam[(s0 * K + q) * n + i] : 0.0;
+    if (A.dT0) A.dT0[qz] = ok ? (t.sh ? a.lam[(s0 * K + q) * n + N] : a.gt[q]) : 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(128) k_adjoint(AdjParams A) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const unsigned char* blob = A.blob;
+  if (A.blob_in_smem) {
+    const int4* src = reinterpret_cast<const int4*>(A.blob);
+    int4* dst = reinterpret_cast<int4*>(sm);
+    for (int i = threadIdx.x; i < A.blob_bytes / 16; i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+    blob = sm;
+  }
+  const Net t = make_net(blob);
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  double* lane_base = A.ws + warp * A.lane_doubles * WS_LANES + lane;
+  const WS w = make_ws(t, lane_base);
+  const AWS a = make_aws(A, lane_base);
+  AdjZone Zs;
+  Zs.z = -1;
+  Zs.s = -1;
+  bool active = false, retired = false, fresh = false;
+  for (;;) {
+    const unsigned need = __ballot_sync(0xffffffffu, !active && !retired);
+    if (need) {
+      const int leader = __ffs(need) - 1;
+      unsigned long long base = 0;
+      if (lane == leader) base = atomicAdd(A.queue, (unsigned long long)__popc(need));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (!active && !retired) {
+        const unsigned long long z = base + __popc(need & ((1u << lane) - 1u));
+        if (z < (unsigned long long)A.Z) {
+          Zs.z = (long long)z;
+          active = true;
+          fresh = true;
+        } else {
+          retired = true;
+        }
+      }
+    }
+    if (__all_sync(0xffffffffu, retired)) break;
+    if (active) {
+      bool done;
+      if (fresh) {
+        done = adj_init(t, Zs, w, a, A);
+        fresh = false;
+      } else {
+        done = adj_step(t, Zs, w, a, A);
+      }
+      if (done) {
+        adj_finish(t, Zs, a, A);
+        active = false;
+      }
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" int nb_burn_adjoint(nb_net net, void* tape, int32_t K, const double* gY,
+                               const double* gE, const double* gT9, double* d_ln_mult,
+                               double* dY0, double* dT0, void* stream) {
+  if (!net || !tape || K < 1 || K > 64 || !gY || !d_ln_mult) return NB_E_ARG;
+  nb_tape_s* tp = (nb_tape_s*)tape;
+  if (tp->magic != 0x7a9e5eedu || tp->net != net || !tp->recorded) return NB_E_TAPE;
+  const BlobHeader& h = net->h;
+  const long long Z = tp->recZ;
+  if (Z == 0) return NB_OK;
+  AdjParams A;
+  std::memset(&A, 0, sizeof(A));
+  A.blob = net->d_blob;
+  A.blob_bytes = h.bytes;
+  A.Z = Z;
+  A.K = K;
+  A.tape = tp->dev;
+  A.lnm = tp->has_lnm ? tp->lnm : nullptr;
+  A.lnm_per_zone = tp->lnm_per_zone;
+  A.gY = gY; A.gE = gE; A.gT9 = gT9;
+  A.dl = d_ln_mult; A.dY0 = dY0; A.dT0 = dT0;
+  const int n = h.n;
+  long long off = h.lane_doubles;
+  A.o_lam = (int)off; off += (long long)HMAX * K * n;
+  A.o_ee = (int)off; off += (long long)HMAX * K;
+  A.o_gr = (int)off; off += (long long)K * h.R;
+  A.o_gt = (int)off; off += K;
+  A.o_mu = (int)off; off += n;
+  A.o_de = (int)off; off += n;
+  A.lane_doubles = off;
+  const int tpb = 128;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::lock_guard<std::mutex> lk(net->mu);
+  const size_t smem = (size_t)h.bytes;
+  const int in_smem = smem <= 96 * 1024 ? 1 : 0;
+  const size_t dyn = in_smem ? smem : 0;
+  if (dyn > 48 * 1024)
+    CK(cudaFuncSetAttribute(k_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+  int occ = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_adjoint, tpb, dyn));
+  long long blocks = (long long)std::max(1, std::min(occ, 4)) * net->sm_count;
+  const long long needed = (Z + tpb - 1) / tpb;
+  if (blocks > needed) blocks = needed;
+  const size_t need = (size_t)blocks * tpb * A.lane_doubles * sizeof(double);
+  int rc = nb::ensure((void**)&net->ws_adj, &net->ws_adj_bytes, need);
+  if (rc) return rc;
+  A.ws = net->ws_adj;
+  A.queue = net->queue + 1;   // a second counter in the same allocation
+  A.blob_in_smem = in_smem;
+  CK(cudaMemsetAsync(A.queue, 0, sizeof(unsigned long long), st));
+  k_adjoint<<<(unsigned)blocks, tpb, dyn, st>>>(A);
+  CK(cudaGetLastError());
+  return NB_OK;
+}

@@ -1,0 +1,409 @@
+// burn.cu -- kernels and C ABI of the batched reaction-network burn.
+//
+// Two launch shapes run the same per-zone integrator (device.cuh):
+//  * persistent: a grid sized to the GPU (blocks_per_sm x SMs); every lane
+//    claims zones from a device work queue and claims the next one as soon as
+//    its zone finishes, so zones needing 10 or 10^4 steps share warps without
+//    idling the FP64 pipe;
+//  * plain: one thread per zone, one launch over all zones (the comparison
+//    launch).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "blob.h"
+#include "device.cuh"
+#include "../../include/netburn.h"
+
+namespace nb {
+int build_blob(const nb_topology* T, const double* coeffs,
+               std::vector<uint8_t>* out, BlobHeader* hdr_out);
+}
+
+using namespace nb;
+
+// ------------------------------------------------------------------ kernels
+
+__global__ void __launch_bounds__(128) k_burn_persistent(BurnParams P) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const unsigned char* blob = P.blob;
+  if (P.blob_in_smem) {
+    const int4* src = reinterpret_cast<const int4*>(P.blob);
+    int4* dst = reinterpret_cast<int4*>(sm);
+    for (int i = threadIdx.x; i < P.blob_bytes / 16; i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+    blob = sm;
+  }
+  const Net t = make_net(blob);
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  double* lane_base = P.ws + warp * (long long)t.lane_doubles * WS_LANES + lane;
+  const WS w = make_ws(t, lane_base);
+  Zone s;
+  s.z = -1;
+  bool active = false, retired = false, fresh = false;
+  for (;;) {
+    const unsigned need = __ballot_sync(0xffffffffu, !active && !retired);
+    if (need) {
+      const int leader = __ffs(need) - 1;
+      unsigned long long base = 0;
+      if (lane == leader) base = atomicAdd(P.queue, (unsigned long long)__popc(need));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (!active && !retired) {
+        const unsigned long long z = base + __popc(need & ((1u << lane) - 1u));
+        if (z < (unsigned long long)P.Z) {
+          s.z = (long long)z;
+          active = true;
+          fresh = true;
+        } else {
+          retired = true;
+        }
+      }
+    }
+    if (__all_sync(0xffffffffu, retired)) break;
+    if (active) {
+      bool done;
+      if (fresh) {
+        done = zone_init(t, s, w, P);
+        fresh = false;
+      } else {
+        done = zone_attempt(t, s, w, P);
+      }
+      if (done) {
+        zone_finish(t, s, w, P);
+        active = false;
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(128) k_burn_plain(BurnParams P) {
+  const Net t = make_net(P.blob);
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= P.Z) return;
+  const int lane = threadIdx.x & 31;
+  double* lane_base = P.ws + (gid >> 5) * (long long)t.lane_doubles * WS_LANES + lane;
+  const WS w = make_ws(t, lane_base);
+  Zone s;
+  s.z = gid;
+  bool done = zone_init(t, s, w, P);
+  while (!done) done = zone_attempt(t, s, w, P);
+  zone_finish(t, s, w, P);
+}
+
+// ------------------------------------------------------------------ host side
+
+#include "host.h"
+
+extern "C" {
+
+void nb_default_options(nb_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->max_attempts = 500000;
+  o->kernel = NB_KERNEL_PERSISTENT;
+  o->threads_per_block = 0;
+  o->blocks_per_sm = 0;
+  o->blob_in_shared = -1;
+}
+
+const char* nb_strerror(int code) {
+  switch (code) {
+    case NB_OK: return "ok";
+    case NB_E_ARG: return "bad argument";
+    case NB_E_TOPOLOGY: return "bad topology (species index out of range or empty reaction)";
+    case NB_E_TOO_LARGE: return "network exceeds the compiled limits";
+    case NB_E_CUDA: return "CUDA runtime error";
+    case NB_E_NOMEM: return "allocation failed";
+    case NB_E_TAPE: return "tape missing, too small or from another network";
+    default: return "unknown error";
+  }
+}
+
+int nb_net_load(const nb_topology* T, const double* coeffs, nb_net* out) {
+  if (!T || !out || (T->n_reactions > 0 && (!coeffs || !T->reactants || !T->products)))
+    return NB_E_ARG;
+  *out = nullptr;
+  const int N = T->n_species, R = T->n_reactions;
+  if (N < 1 || R < 0) return NB_E_ARG;
+  if (T->self_heating && !T->Q) return NB_E_ARG;
+  for (int r = 0; r < R; ++r) {
+    int nre = 0;
+    for (int s = 0; s < 3; ++s) {
+      const int a = T->reactants[3 * r + s], b = T->products[3 * r + s];
+      if (a < -1 || a >= N || b < -1 || b >= N) return NB_E_TOPOLOGY;
+      nre += a >= 0;
+    }
+    if (nre == 0) return NB_E_TOPOLOGY;
+    for (int j = 0; j < 7; ++j)
+      if (!std::isfinite(coeffs[7 * r + j])) return NB_E_ARG;
+    if (T->Q && !std::isfinite(T->Q[r])) return NB_E_ARG;
+    if (T->scale && !std::isfinite(T->scale[r])) return NB_E_ARG;
+  }
+  nb_net net = new (std::nothrow) nb_net_s();
+  if (!net) return NB_E_NOMEM;
+  int rc = build_blob(T, coeffs, &net->blob, &net->h);
+  if (rc != NB_OK) { delete net; return rc; }
+  if (cudaGetDevice(&net->device) != cudaSuccess) { delete net; return NB_E_CUDA; }
+  cudaDeviceGetAttribute(&net->sm_count, cudaDevAttrMultiProcessorCount, net->device);
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, net->device);
+  net->smem_optin = (size_t)optin;
+  if (cudaMalloc(&net->d_blob, net->blob.size()) != cudaSuccess ||
+      cudaMemcpy(net->d_blob, net->blob.data(), net->blob.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMalloc(&net->queue, 256) != cudaSuccess) {
+    if (net->d_blob) cudaFree(net->d_blob);
+    if (net->queue) cudaFree(net->queue);
+    delete net;
+    return NB_E_CUDA;
+  }
+  *out = net;
+  return NB_OK;
+}
+
+int nb_net_free(nb_net net) {
+  if (!net) return NB_E_ARG;
+  cudaFree(net->d_blob);
+  cudaFree(net->queue);
+  if (net->ws) cudaFree(net->ws);
+  if (net->stage) cudaFree(net->stage);
+  delete net;
+  return NB_OK;
+}
+
+int nb_net_get_info(nb_net net, nb_net_info* o) {
+  if (!net || !o) return NB_E_ARG;
+  const BlobHeader& h = net->h;
+  std::memset(o, 0, sizeof(*o));
+  o->n_state = h.n;
+  o->n_reactions = h.R;
+  o->nnz_jacobian = h.nnz_jac;
+  o->nnz_lu = h.nnz;
+  o->n_dterms = h.nd;
+  o->lane_doubles = h.lane_doubles;
+  o->blob_bytes = h.bytes;
+  o->has_energy = h.has_E;
+  o->flops_rate_eval = h.fl_teval;
+  o->flops_rate_deriv = h.fl_teval_g;
+  o->flops_terms = h.fl_terms;
+  o->flops_tsolve = h.fl_tsolve;
+  o->flops_rhs = h.fl_rhs;
+  o->flops_jacobian = h.fl_jac;
+  o->flops_lu = h.fl_lu;
+  o->flops_solve = h.fl_solve;
+  o->flops_edot = h.fl_edot;
+  o->exp_per_rate_eval = h.n_exp_per_teval;
+  return NB_OK;
+}
+
+}  // extern "C"
+
+// Launch one burn (device pointers).  Caller holds net->mu.
+static int launch_burn(nb_net net, BurnParams& P, const nb_options& o,
+                       cudaStream_t st) {
+  const int tpb = o.threads_per_block > 0 ? o.threads_per_block : 128;
+  if (tpb % 32 != 0 || tpb > 128) return NB_E_ARG;
+  const size_t lane_bytes = (size_t)net->h.lane_doubles * sizeof(double);
+  P.blob = net->d_blob;
+  P.blob_bytes = net->h.bytes;
+  if (o.kernel == NB_KERNEL_PLAIN) {
+    const long long blocks = (P.Z + tpb - 1) / tpb;
+    const size_t need = (size_t)blocks * tpb * lane_bytes;
+    int rc = nb::ensure((void**)&net->ws, &net->ws_bytes, need);
+    if (rc) return rc;
+    P.ws = net->ws;
+    P.blob_in_smem = 0;
+    k_burn_plain<<<(unsigned)blocks, tpb, 0, st>>>(P);
+    CK(cudaGetLastError());
+    return NB_OK;
+  }
+  int in_smem = o.blob_in_shared;
+  const size_t smem = (size_t)net->h.bytes;
+  if (in_smem < 0) in_smem = smem <= 96 * 1024 ? 1 : 0;
+  if (in_smem && smem > net->smem_optin) return NB_E_TOO_LARGE;
+  const size_t dyn = in_smem ? smem : 0;
+  if (dyn > 48 * 1024)
+    CK(cudaFuncSetAttribute(k_burn_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+  int bps = o.blocks_per_sm;
+  if (bps <= 0) {
+    int occ = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_burn_persistent, tpb, dyn));
+    bps = std::max(1, std::min(occ, 512 / tpb));
+  }
+  long long blocks = (long long)bps * net->sm_count;
+  const long long needed_blocks = (P.Z + tpb - 1) / tpb;
+  if (blocks > needed_blocks) blocks = needed_blocks;
+  const size_t need = (size_t)blocks * tpb * lane_bytes;
+  int rc = nb::ensure((void**)&net->ws, &net->ws_bytes, need);
+  if (rc) return rc;
+  P.ws = net->ws;
+  P.queue = net->queue;
+  P.blob_in_smem = in_smem;
+  CK(cudaMemsetAsync(net->queue, 0, sizeof(unsigned long long), st));
+  k_burn_persistent<<<(unsigned)blocks, tpb, dyn, st>>>(P);
+  CK(cudaGetLastError());
+  return NB_OK;
+}
+
+static int check_burn_args(long long Z, double t_end, double rtol, double atol) {
+  if (Z < 0) return NB_E_ARG;
+  if (!(rtol > 0.0) || !(atol > 0.0) || !(t_end >= 0.0) || !std::isfinite(t_end))
+    return NB_E_ARG;
+  return NB_OK;
+}
+
+extern "C" int nb_burn_batch(nb_net net, int64_t Z, const double* Y0, const double* T9_0,
+                             const double* rho, double t_end, double rtol, double atol,
+                             const double* ln_mult, int32_t ln_mult_per_zone, double* Y,
+                             double* T9, double* E, int32_t* counters, int32_t* status,
+                             const nb_options* opt, void* tape, void* stream) {
+  if (!net) return NB_E_ARG;
+  int rc = check_burn_args(Z, t_end, rtol, atol);
+  if (rc) return rc;
+  if (Z == 0) return NB_OK;
+  if (!Y0 || !T9_0 || !rho || !Y || !T9 || !status) return NB_E_ARG;
+  nb_options o;
+  nb_default_options(&o);
+  if (opt) o = *opt;
+  if (o.max_attempts <= 0) return NB_E_ARG;
+  BurnParams P;
+  std::memset(&P, 0, sizeof(P));
+  P.Z = Z; P.Y0 = Y0; P.T9_0 = T9_0; P.rho = rho;
+  P.t_end = t_end; P.rtol = rtol; P.atol = atol;
+  P.lnm = ln_mult; P.lnm_per_zone = ln_mult_per_zone ? 1 : 0;
+  P.Y = Y; P.T9 = T9; P.E = E; P.counters = counters; P.status = status;
+  P.max_attempts = o.max_attempts;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::lock_guard<std::mutex> lk(net->mu);
+  if (tape) {
+    nb_tape_s* tp = (nb_tape_s*)tape;
+    if (tp->magic != 0x7a9e5eedu || tp->net != net || tp->Z < Z) return NB_E_TAPE;
+    P.use_tape = 1;
+    P.tape = tp->dev;
+    tp->recZ = Z;
+    tp->recorded = 1;
+    tp->t_end = t_end; tp->rtol = rtol; tp->atol = atol;
+    tp->has_lnm = ln_mult != nullptr;
+    tp->lnm_per_zone = P.lnm_per_zone;
+    if (ln_mult) {
+      const size_t cnt = (size_t)(P.lnm_per_zone ? Z : 1) * net->h.R;
+      CK(cudaMemcpyAsync(tp->lnm, ln_mult, cnt * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    }
+  }
+  return launch_burn(net, P, o, st);
+}
+
+extern "C" int nb_burn_batch_host(nb_net net, int64_t Z, const double* Y0,
+                                  const double* T9_0, const double* rho, double t_end,
+                                  double rtol, double atol, const double* ln_mult,
+                                  int32_t ln_mult_per_zone, double* Y, double* T9,
+                                  double* E, int32_t* counters, int32_t* status,
+                                  const nb_options* opt, void* stream) {
+  if (!net) return NB_E_ARG;
+  int rc = check_burn_args(Z, t_end, rtol, atol);
+  if (rc) return rc;
+  if (Z == 0) return NB_OK;
+  if (!Y0 || !T9_0 || !rho || !Y || !T9 || !status) return NB_E_ARG;
+  nb_options o;
+  nb_default_options(&o);
+  if (opt) o = *opt;
+  if (o.max_attempts <= 0) return NB_E_ARG;
+  const int N = net->h.N, R = net->h.R;
+  const size_t zN = (size_t)Z * N * 8, z8 = (size_t)Z * 8, z4 = (size_t)Z * 4;
+  const size_t nl = ln_mult ? (size_t)(ln_mult_per_zone ? Z : 1) * R * 8 : 0;
+  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  const size_t off_Y0 = 0, off_T0 = off_Y0 + al(zN), off_rho = off_T0 + al(z8),
+               off_l = off_rho + al(z8), off_Y = off_l + al(nl), off_T = off_Y + al(zN),
+               off_E = off_T + al(z8), off_c = off_E + al(z8),
+               off_s = off_c + al(z4 * NCOUNT), total = off_s + al(z4);
+  cudaStream_t st = (cudaStream_t)stream;
+  std::lock_guard<std::mutex> lk(net->mu);
+  rc = nb::ensure((void**)&net->stage, &net->stage_bytes, total);
+  if (rc) return rc;
+  unsigned char* b = net->stage;
+  CK(cudaMemcpyAsync(b + off_Y0, Y0, zN, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(b + off_T0, T9_0, z8, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(b + off_rho, rho, z8, cudaMemcpyHostToDevice, st));
+  if (nl) CK(cudaMemcpyAsync(b + off_l, ln_mult, nl, cudaMemcpyHostToDevice, st));
+  BurnParams P;
+  std::memset(&P, 0, sizeof(P));
+  P.Z = Z;
+  P.Y0 = (const double*)(b + off_Y0);
+  P.T9_0 = (const double*)(b + off_T0);
+  P.rho = (const double*)(b + off_rho);
+  P.t_end = t_end; P.rtol = rtol; P.atol = atol;
+  P.lnm = nl ? (const double*)(b + off_l) : nullptr;
+  P.lnm_per_zone = ln_mult_per_zone ? 1 : 0;
+  P.Y = (double*)(b + off_Y);
+  P.T9 = (double*)(b + off_T);
+  P.E = (double*)(b + off_E);
+  P.counters = (int32_t*)(b + off_c);
+  P.status = (int32_t*)(b + off_s);
+  P.max_attempts = o.max_attempts;
+  rc = launch_burn(net, P, o, st);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(Y, b + off_Y, zN, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(T9, b + off_T, z8, cudaMemcpyDeviceToHost, st));
+  if (E) CK(cudaMemcpyAsync(E, b + off_E, z8, cudaMemcpyDeviceToHost, st));
+  if (counters) CK(cudaMemcpyAsync(counters, b + off_c, z4 * NCOUNT, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(status, b + off_s, z4, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return NB_OK;
+}
+
+// ------------------------------------------------------------------ tape
+
+extern "C" int nb_tape_alloc(nb_net net, int64_t Z, int32_t max_steps, void** tape) {
+  if (!net || !tape || Z <= 0 || max_steps < 1) return NB_E_ARG;
+  *tape = nullptr;
+  nb_tape_s* tp = new (std::nothrow) nb_tape_s();
+  if (!tp) return NB_E_NOMEM;
+  tp->net = net;
+  tp->Z = Z;
+  tp->cap = max_steps + 1;
+  const int n = net->h.n;
+  const size_t rec = (size_t)Z * tp->cap * (n + 3) * sizeof(double);
+  const size_t ord = (size_t)Z * tp->cap;
+  bool ok = cudaMalloc(&tp->dev.rec, rec) == cudaSuccess &&
+            cudaMalloc(&tp->dev.ord, ord) == cudaSuccess &&
+            cudaMalloc(&tp->dev.steps, (size_t)Z * 4) == cudaSuccess &&
+            cudaMalloc(&tp->dev.zstat, (size_t)Z * 4) == cudaSuccess &&
+            cudaMalloc(&tp->dev.rho, (size_t)Z * 8) == cudaSuccess &&
+            cudaMalloc(&tp->dev.T9f, (size_t)Z * 8) == cudaSuccess &&
+            cudaMalloc(&tp->lnm, (size_t)Z * std::max(net->h.R, 1) * 8) == cudaSuccess;
+  tp->dev.cap = tp->cap;
+  if (!ok) {
+    cudaFree(tp->dev.rec); cudaFree(tp->dev.ord); cudaFree(tp->dev.steps);
+    cudaFree(tp->dev.zstat); cudaFree(tp->dev.rho); cudaFree(tp->dev.T9f);
+    cudaFree(tp->lnm);
+    delete tp;
+    return NB_E_NOMEM;
+  }
+  *tape = tp;
+  return NB_OK;
+}
+
+extern "C" int nb_tape_free(void* tape) {
+  nb_tape_s* tp = (nb_tape_s*)tape;
+  if (!tp || tp->magic != 0x7a9e5eedu) return NB_E_ARG;
+  cudaFree(tp->dev.rec); cudaFree(tp->dev.ord); cudaFree(tp->dev.steps);
+  cudaFree(tp->dev.zstat); cudaFree(tp->dev.rho); cudaFree(tp->dev.T9f);
+  cudaFree(tp->lnm);
+  tp->magic = 0;
+  delete tp;
+  return NB_OK;
+}
+
+extern "C" int nb_tape_steps(void* tape, const int32_t** steps) {
+  nb_tape_s* tp = (nb_tape_s*)tape;
+  if (!tp || tp->magic != 0x7a9e5eedu || !steps) return NB_E_ARG;
+  *steps = tp->dev.steps;
+  return NB_OK;
+}
+

@@ -1,0 +1,65 @@
+// host.h -- host-side objects behind the C ABI handles (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <mutex>
+#include <vector>
+
+#include "blob.h"
+#include "device.cuh"
+#include "../../include/netburn.h"
+
+struct nb_net_s {
+  nb::BlobHeader h;
+  std::vector<uint8_t> blob;
+  unsigned char* d_blob = nullptr;
+  int device = 0;
+  int sm_count = 0;
+  size_t smem_optin = 0;
+  double* ws = nullptr;
+  size_t ws_bytes = 0;
+  unsigned long long* queue = nullptr;
+  // staging for the host-pointer entry point
+  unsigned char* stage = nullptr;
+  size_t stage_bytes = 0;
+  double* ws_adj = nullptr;   // adjoint per-lane workspace
+  size_t ws_adj_bytes = 0;
+  std::mutex mu;
+};
+
+struct nb_tape_s {
+  nb_net net;
+  long long Z;
+  int cap;
+  nb::TapeDev dev;
+  long long recZ = 0;       // zones of the recorded burn
+  double* lnm = nullptr;   // copy of the multipliers of the recorded burn
+  int lnm_per_zone = 0;
+  int has_lnm = 0;
+  double t_end = 0, rtol = 0, atol = 0;
+  int recorded = 0;
+  unsigned magic = 0x7a9e5eedu;
+};
+
+#define CK(call)                                                   \
+  do {                                                             \
+    cudaError_t e_ = (call);                                       \
+    if (e_ != cudaSuccess) return NB_E_CUDA;                       \
+  } while (0)
+
+
+namespace nb {
+// (Re)allocate a device buffer of at least `need` bytes.
+inline int ensure(void** p, size_t* have, size_t need) {
+  if (*have >= need && *p) return NB_OK;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *have = 0;
+  if (cudaMalloc(p, need) != cudaSuccess) {
+    *p = nullptr;
+    return NB_E_NOMEM;
+  }
+  *have = need;
+  return NB_OK;
+}
+}  // namespace nb
