@@ -169,11 +169,21 @@ def run_native(args):
             dist.barrier()
             torch.cuda.synchronize()
 
+    if args.blocks_per_sm or args.threads_per_block or args.ws_in_shared >= 0:
+        launch = dict(blocks_per_sm=args.blocks_per_sm,
+                      threads_per_block=args.threads_per_block,
+                      ws_in_shared=args.ws_in_shared)
+        tune_ms = None
+    else:
+        from paper_2312_02836_gb300.autotune import autotune
+        launch = autotune(netc, Y0, T9, rho, s["t_end"], s["rtol"], s["atol"])
+        tune_ms = launch.pop("_timings_ms")
+
     def step(kernel="persistent"):
         nonlocal out
+        opts = launch if kernel == "persistent" else {}
         out = nb.burn(netc, Y0, T9, rho, s["t_end"], s["rtol"], s["atol"],
-                      kernel=kernel, out=out, blocks_per_sm=args.blocks_per_sm,
-                      threads_per_block=args.threads_per_block)
+                      kernel=kernel, out=out, **opts)
 
     for _ in range(args.warmup):
         step()
@@ -212,13 +222,14 @@ def run_native(args):
                 E=torch.empty(Z, dtype=torch.float64).pin_memory().numpy(),
                 counters=torch.empty((Z, 8), dtype=torch.int32).pin_memory().numpy(),
                 status=torch.empty(Z, dtype=torch.int32).pin_memory().numpy())
-    nb.burn_host(netc, hY0, hT9, hrho, s["t_end"], s["rtol"], s["atol"], out=hout)
+    nb.burn_host(netc, hY0, hT9, hrho, s["t_end"], s["rtol"], s["atol"], out=hout, **launch)
     e2e_t = []
     for _ in range(max(2, min(args.steps, 5))):
         flush.fill_(1.0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        nb.burn_host(netc, hY0, hT9, hrho, s["t_end"], s["rtol"], s["atol"], out=hout)
+        nb.burn_host(netc, hY0, hT9, hrho, s["t_end"], s["rtol"], s["atol"], out=hout,
+                     **launch)
         e2e_t.append(time.perf_counter() - t0)
     assert np.array_equal(hout["Y"], out.Y.cpu().numpy())
     h2d = hY0.nbytes + hT9.nbytes + hrho.nbytes
@@ -268,7 +279,10 @@ def run_native(args):
             "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD_DESC, "zones_per_gpu": Z,
                        "l2": "256 MiB buffer written between timed steps (L2 flush)",
-                       "kernel": "persistent lane-per-zone, device work queue"},
+                       "kernel": "persistent lane-per-zone, device work queue",
+                       "launch": launch,
+                       "autotune_ms": None if tune_ms is None else
+                       [[c, round(m, 2)] for c, m in tune_ms]},
             "roofline": roofline, "cpu_baseline": base,
             "e2e": {"value": Z / statistics.mean(e2e_t), "unit": "zone-burns/s",
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
@@ -343,6 +357,7 @@ def main():
                    help="override t_end (profiling of a shorter burn only)")
     p.add_argument("--blocks-per-sm", type=int, default=0)
     p.add_argument("--threads-per-block", type=int, default=0)
+    p.add_argument("--ws-in-shared", type=int, default=-1)
     p.add_argument("--cpu-zones", type=int, default=8192)
     p.add_argument("--ref-zones", type=int, default=4096)
     p.add_argument("--no-cpu-baseline", action="store_true")

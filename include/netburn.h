@@ -114,7 +114,10 @@ typedef struct {
   int32_t threads_per_block;/* 0 = library choice */
   int32_t blocks_per_sm;    /* 0 = library choice (persistent kernel) */
   int32_t blob_in_shared;   /* -1 auto, 0 global (L1), 1 shared memory */
-  int32_t reserved[3];
+  int32_t ws_in_shared;     /* persistent kernel: -1 auto, 0 per-zone work
+                               arrays in global memory, 1 the Newton-loop
+                               arrays in shared memory (history stays global) */
+  int32_t reserved[2];
 } nb_options;
 
 #define NB_KERNEL_PERSISTENT 0  /* lane-per-zone, device work queue */
@@ -177,6 +180,14 @@ int nb_tape_steps(void* tape, const int32_t** steps);
 int nb_burn_adjoint(nb_net net, void* tape, int32_t K, const double* gY,
                     const double* gE, const double* gT9, double* d_ln_mult,
                     double* dY0, double* dT0, void* stream);
+
+/* FP64 pipe microbenchmark (a hardware measurement; the paper has no
+ * counterpart).  Runs 8 independent DFMA chains per thread on
+ * blocks_per_sm x SMs blocks of 256 threads, with only `active_lanes` of
+ * each warp working, and returns the useful FP64 rate in TFLOP/s (an FMA
+ * counted as 2).  Synchronous; allocates and frees its own output buffer. */
+int nb_probe_fp64(int32_t active_lanes, int32_t iters, int32_t blocks_per_sm,
+                  double* tflops_useful, double* ms);
 
 const char* nb_strerror(int code);
 

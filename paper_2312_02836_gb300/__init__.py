@@ -22,7 +22,7 @@ from ._abi import (COUNTER_NAMES, KERNEL_PERSISTENT, KERNEL_PLAIN, NCOUNT,
 
 __all__ = ["Network", "burn", "burn_host", "Tape", "adjoint", "Burn",
            "BurnResult", "NetburnError", "COUNTER_NAMES", "ZONE_STATUS",
-           "KERNEL_PERSISTENT", "KERNEL_PLAIN", "library_path"]
+           "KERNEL_PERSISTENT", "KERNEL_PLAIN", "library_path", "probe_fp64"]
 
 
 def library_path() -> str:
@@ -103,7 +103,7 @@ class BurnResult(NamedTuple):
 
 
 def _options(kernel, threads_per_block, blocks_per_sm, blob_in_shared,
-             max_attempts):
+             max_attempts, ws_in_shared=-1):
     o = _abi.Options()
     _abi.load().nb_default_options(C.byref(o))
     if isinstance(kernel, str):
@@ -113,6 +113,7 @@ def _options(kernel, threads_per_block, blocks_per_sm, blob_in_shared,
     o.blocks_per_sm = int(blocks_per_sm)
     o.blob_in_shared = int(blob_in_shared)
     o.max_attempts = int(max_attempts)
+    o.ws_in_shared = int(ws_in_shared)
     return o
 
 
@@ -131,7 +132,8 @@ def _dev(t, torch, name, shape=None):
 def burn(net: Network, Y0, T9, rho, t_end: float, rtol: float, atol: float,
          ln_mult=None, *, kernel="persistent", tape: "Optional[Tape]" = None,
          threads_per_block=0, blocks_per_sm=0, blob_in_shared=-1,
-         max_attempts=500000, stream=None, out: Optional[BurnResult] = None):
+         ws_in_shared=-1, max_attempts=500000, stream=None,
+         out: Optional[BurnResult] = None):
     """Burn Z zones on the GPU.  Y0 [Z,N], T9 [Z], rho [Z] CUDA float64;
     ln_mult None, [R] or [Z,R].  Returns BurnResult of CUDA tensors."""
     torch = _torch()
@@ -156,7 +158,7 @@ def burn(net: Network, Y0, T9, rho, t_end: float, rtol: float, atol: float,
                          torch.empty((Z, NCOUNT), dtype=torch.int32, device=dev),
                          torch.empty((Z,), dtype=torch.int32, device=dev))
     o = _options(kernel, threads_per_block, blocks_per_sm, blob_in_shared,
-                 max_attempts)
+                 max_attempts, ws_in_shared)
     st = stream if stream is not None else torch.cuda.current_stream(dev)
     lib = _abi.load()
     ptr = lambda t: None if t is None else t.data_ptr()
@@ -174,7 +176,8 @@ def burn(net: Network, Y0, T9, rho, t_end: float, rtol: float, atol: float,
 
 def burn_host(net: Network, Y0, T9, rho, t_end, rtol, atol, ln_mult=None, *,
               kernel="persistent", threads_per_block=0, blocks_per_sm=0,
-              blob_in_shared=-1, max_attempts=500000, stream=None, out=None):
+              blob_in_shared=-1, ws_in_shared=-1, max_attempts=500000,
+              stream=None, out=None):
     """Burn from host (numpy) arrays through ``nb_burn_batch_host``: the
     library copies the inputs in, burns and copies the outputs back.
     Returns a dict of numpy arrays; ``out`` may supply preallocated (e.g.
@@ -191,7 +194,7 @@ def burn_host(net: Network, Y0, T9, rho, t_end, rtol, atol, ln_mult=None, *,
                    counters=np.empty((Z, NCOUNT), np.int32),
                    status=np.empty(Z, np.int32))
     o = _options(kernel, threads_per_block, blocks_per_sm, blob_in_shared,
-                 max_attempts)
+                 max_attempts, ws_in_shared)
     st = stream if stream is not None else torch.cuda.current_stream()
     p = lambda a: None if a is None else a.ctypes.data
     rc = _abi.load().nb_burn_batch_host(
@@ -313,6 +316,17 @@ def _autograd():
             return dY0, dT0, None, g_lm, None, None, None, None, None
 
     return Burn
+
+
+def probe_fp64(active_lanes: int = 32, iters: int = 4096, blocks_per_sm: int = 4):
+    """Measured FP64 rate of the current GPU (TFLOP/s, FMA = 2 flops) with
+    `active_lanes` working lanes per warp."""
+    _torch()
+    tf = C.c_double(0.0)
+    ms = C.c_double(0.0)
+    _abi.check(_abi.load().nb_probe_fp64(active_lanes, iters, blocks_per_sm,
+                                         C.byref(tf), C.byref(ms)), "nb_probe_fp64")
+    return tf.value
 
 
 class _LazyBurn:

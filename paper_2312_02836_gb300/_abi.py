@@ -24,7 +24,7 @@ KERNEL_PLAIN = 1
 # every symbol declared in include/netburn.h
 EXPORTS = ("nb_net_load", "nb_net_free", "nb_net_get_info", "nb_default_options",
            "nb_burn_batch", "nb_burn_batch_host", "nb_tape_alloc", "nb_tape_free",
-           "nb_tape_steps", "nb_burn_adjoint", "nb_strerror")
+           "nb_tape_steps", "nb_burn_adjoint", "nb_probe_fp64", "nb_strerror")
 
 
 class Topology(C.Structure):
@@ -50,7 +50,8 @@ class NetInfo(C.Structure):
 class Options(C.Structure):
     _fields_ = [("max_attempts", C.c_int32), ("kernel", C.c_int32),
                 ("threads_per_block", C.c_int32), ("blocks_per_sm", C.c_int32),
-                ("blob_in_shared", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("blob_in_shared", C.c_int32), ("ws_in_shared", C.c_int32),
+                ("reserved", C.c_int32 * 2)]
 
 
 def load(build_if_needed: bool = True):
@@ -75,6 +76,8 @@ def load(build_if_needed: bool = True):
         lib.nb_tape_free.argtypes = [P]
         lib.nb_tape_steps.argtypes = [P, P]
         lib.nb_burn_adjoint.argtypes = [P, P, I32, P, P, P, P, P, P, P]
+        lib.nb_probe_fp64.argtypes = [I32, I32, I32, P, P]
+        lib.nb_probe_fp64.restype = C.c_int
         lib.nb_strerror.argtypes = [C.c_int]
         lib.nb_strerror.restype = C.c_char_p
         for name in ("nb_net_load", "nb_net_free", "nb_net_get_info",

@@ -1,0 +1,70 @@
+"""Launch-shape autotuner for the persistent burn kernel.
+
+The kernel maps one zone to one lane, so the tunables are how many zones are
+in flight per SM and where their work arrays live:
+
+* ``ws_in_shared`` 1: the Newton-loop arrays of every warp in shared memory
+  (history in global memory); 0: everything in the global workspace;
+* ``threads_per_block`` and ``blocks_per_sm``: zones in flight.  Fewer lanes
+  than zones let the device queue refill lanes whose zone finished; more
+  lanes hide more latency but grow the workspace beyond L2.
+
+Each candidate burns the caller's zones once and is timed with CUDA events
+on the current stream; the fastest wins.  Results are cached per network,
+device and zone count for the life of the process.
+"""
+from __future__ import annotations
+
+from typing import Optional
+
+_CACHE: dict = {}
+
+DEFAULT_CANDIDATES = (
+    dict(ws_in_shared=1, threads_per_block=32, blocks_per_sm=3),
+    dict(ws_in_shared=1, threads_per_block=32, blocks_per_sm=2),
+    dict(ws_in_shared=1, threads_per_block=64, blocks_per_sm=1),
+    dict(ws_in_shared=0, threads_per_block=128, blocks_per_sm=1),
+    dict(ws_in_shared=0, threads_per_block=64, blocks_per_sm=2),
+    dict(ws_in_shared=0, threads_per_block=128, blocks_per_sm=2),
+    dict(ws_in_shared=0, threads_per_block=64, blocks_per_sm=3),
+)
+
+
+def autotune(net, Y0, T9, rho, t_end, rtol, atol, ln_mult=None, *,
+             candidates=DEFAULT_CANDIDATES, key: Optional[str] = None,
+             verbose: bool = False) -> dict:
+    """Return the fastest launch options for burning these zones."""
+    import torch
+
+    from . import NetburnError, burn
+
+    dev = Y0.device
+    ck = (key or id(net), torch.cuda.get_device_name(dev), int(Y0.shape[0]))
+    if ck in _CACHE:
+        return dict(_CACHE[ck])
+    stream = torch.cuda.current_stream(dev)
+    best, best_ms, timings = None, float("inf"), []
+    out = None
+    for cand in candidates:
+        try:
+            out = burn(net, Y0, T9, rho, t_end, rtol, atol, ln_mult, out=out, **cand)
+        except NetburnError:
+            continue                      # does not fit this network / GPU
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        burn(net, Y0, T9, rho, t_end, rtol, atol, ln_mult, out=out, **cand)
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b)
+        timings.append((cand, ms))
+        if verbose:
+            print("autotune", cand, f"{ms:.1f} ms")
+        if ms < best_ms:
+            best, best_ms = cand, ms
+    if best is None:
+        raise NetburnError("no launch shape fits this network")
+    _CACHE[ck] = dict(best)
+    result = dict(best)
+    result["_timings_ms"] = [(dict(c), m) for c, m in timings]
+    return result

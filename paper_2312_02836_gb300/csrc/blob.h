@@ -78,7 +78,7 @@ struct BlobHeader {
   int64_t fl_teval, fl_teval_g, fl_terms, fl_rhs, fl_jac, fl_lu, fl_solve,
       fl_edot, fl_tsolve;
   int32_t n_exp_per_teval;
-  int32_t pad_;
+  int32_t hot_doubles;  // leading part of the per-lane layout kept hot
 };
 
 }  // namespace nb

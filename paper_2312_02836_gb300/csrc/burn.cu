@@ -30,6 +30,10 @@ using namespace nb;
 
 // ------------------------------------------------------------------ kernels
 
+// SPLIT = false: the whole per-lane workspace in global memory.
+// SPLIT = true: the Newton-loop arrays ("hot") of every warp in shared memory
+// after the (optional) blob copy, the history in global memory.
+template <bool SPLIT>
 __global__ void __launch_bounds__(128) k_burn_persistent(BurnParams P) {
   extern __shared__ __align__(16) unsigned char sm[];
   const unsigned char* blob = P.blob;
@@ -43,8 +47,15 @@ __global__ void __launch_bounds__(128) k_burn_persistent(BurnParams P) {
   const Net t = make_net(blob);
   const int lane = threadIdx.x & 31;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  double* lane_base = P.ws + warp * (long long)t.lane_doubles * WS_LANES + lane;
-  const WS w = make_ws(t, lane_base);
+  WS w;
+  if (SPLIT) {
+    double* hot = reinterpret_cast<double*>(sm + (P.blob_in_smem ? P.blob_bytes : 0)) +
+                  (size_t)(threadIdx.x >> 5) * t.hot_doubles * WS_LANES + lane;
+    double* cold = P.ws + warp * (long long)(t.lane_doubles - t.hot_doubles) * WS_LANES + lane;
+    w = make_ws_split(t, hot, cold);
+  } else {
+    w = make_ws(t, P.ws + warp * (long long)t.lane_doubles * WS_LANES + lane);
+  }
   Zone s;
   s.z = -1;
   bool active = false, retired = false, fresh = false;
@@ -207,7 +218,10 @@ int nb_net_get_info(nb_net net, nb_net_info* o) {
 // Launch one burn (device pointers).  Caller holds net->mu.
 static int launch_burn(nb_net net, BurnParams& P, const nb_options& o,
                        cudaStream_t st) {
-  const int tpb = o.threads_per_block > 0 ? o.threads_per_block : 128;
+  const size_t hot_warp0 = (size_t)net->h.hot_doubles * WS_LANES * sizeof(double);
+  const bool split0 = o.kernel != NB_KERNEL_PLAIN &&
+                      (o.ws_in_shared > 0 || (o.ws_in_shared < 0 && hot_warp0 <= 64 * 1024));
+  const int tpb = o.threads_per_block > 0 ? o.threads_per_block : (split0 ? 32 : 128);
   if (tpb % 32 != 0 || tpb > 128) return NB_E_ARG;
   const size_t lane_bytes = (size_t)net->h.lane_doubles * sizeof(double);
   P.blob = net->d_blob;
@@ -224,29 +238,36 @@ static int launch_burn(nb_net net, BurnParams& P, const nb_options& o,
     return NB_OK;
   }
   int in_smem = o.blob_in_shared;
-  const size_t smem = (size_t)net->h.bytes;
-  if (in_smem < 0) in_smem = smem <= 96 * 1024 ? 1 : 0;
-  if (in_smem && smem > net->smem_optin) return NB_E_TOO_LARGE;
-  const size_t dyn = in_smem ? smem : 0;
+  const size_t blob_b = (size_t)net->h.bytes;
+  const size_t hot_warp = (size_t)net->h.hot_doubles * WS_LANES * sizeof(double);
+  int split = o.ws_in_shared;
+  if (split < 0) split = hot_warp <= 64 * 1024 ? 1 : 0;
+  if (in_smem < 0) in_smem = blob_b <= 96 * 1024 && (!split || blob_b + hot_warp <= 160 * 1024);
+  size_t dyn = in_smem ? blob_b : 0;
+  if (split) dyn += (size_t)(tpb / 32) * hot_warp;
+  if (dyn > net->smem_optin) return NB_E_TOO_LARGE;
+  auto kfun = split ? k_burn_persistent<true> : k_burn_persistent<false>;
   if (dyn > 48 * 1024)
-    CK(cudaFuncSetAttribute(k_burn_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    CK(cudaFuncSetAttribute(kfun, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
   int bps = o.blocks_per_sm;
-  if (bps <= 0) {
-    int occ = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_burn_persistent, tpb, dyn));
-    bps = std::max(1, std::min(occ, 512 / tpb));
-  }
+  int occ = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfun, tpb, dyn));
+  if (occ < 1) return NB_E_TOO_LARGE;
+  if (bps <= 0) bps = std::min(occ, 512 / tpb);
+  bps = std::max(1, std::min(bps, occ));
   long long blocks = (long long)bps * net->sm_count;
   const long long needed_blocks = (P.Z + tpb - 1) / tpb;
   if (blocks > needed_blocks) blocks = needed_blocks;
-  const size_t need = (size_t)blocks * tpb * lane_bytes;
+  const size_t per_lane = split ? lane_bytes - (size_t)net->h.hot_doubles * sizeof(double)
+                                : lane_bytes;
+  const size_t need = std::max<size_t>((size_t)blocks * tpb * per_lane, 256);
   int rc = nb::ensure((void**)&net->ws, &net->ws_bytes, need);
   if (rc) return rc;
   P.ws = net->ws;
   P.queue = net->queue;
   P.blob_in_smem = in_smem;
   CK(cudaMemsetAsync(net->queue, 0, sizeof(unsigned long long), st));
-  k_burn_persistent<<<(unsigned)blocks, tpb, dyn, st>>>(P);
+  kfun<<<(unsigned)blocks, tpb, dyn, st>>>(P);
   CK(cudaGetLastError());
   return NB_OK;
 }

@@ -12,6 +12,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "blob.h"
 #include "../../include/netburn.h"
@@ -40,7 +41,7 @@ struct Net {
   const Pivot* piv;
   const TriRow *fw, *bw, *tfw, *tbw;
   int w_x, w_xp, w_psi, w_d, w_f, w_iw, w_tmp, w_f0, w_xh, w_eh, w_th, w_k,
-      w_g, w_rr, w_dt, w_lu, lane_doubles;
+      w_g, w_rr, w_dt, w_lu, lane_doubles, hot_doubles;
 };
 
 template <class T>
@@ -79,13 +80,37 @@ NB_HD inline Net make_net(const unsigned char* b) {
   t.w_xh = h->w_xh; t.w_eh = h->w_eh; t.w_th = h->w_th; t.w_k = h->w_k;
   t.w_g = h->w_g; t.w_rr = h->w_rr; t.w_dt = h->w_dt; t.w_lu = h->w_lu;
   t.lane_doubles = h->lane_doubles;
+  t.hot_doubles = h->hot_doubles;
   return t;
 }
 
-// Views of one lane's workspace.
+// Views of one lane's workspace.  The arrays before hot_doubles may live in
+// shared memory (hot_base) while the rest stay in global memory (cold_base,
+// offsets relative to hot_doubles).
 struct WS {
   LV x, xp, psi, d, f, iw, tmp, f0, xh, eh, th, k, g, rr, dt, lu;
 };
+
+NB_HD __forceinline__ WS make_ws_split(const Net& t, double* hot_base, double* cold_base) {
+  WS w;
+  w.x.p = hot_base + t.w_x * WS_LANES;
+  w.xp.p = hot_base + t.w_xp * WS_LANES;
+  w.psi.p = hot_base + t.w_psi * WS_LANES;
+  w.d.p = hot_base + t.w_d * WS_LANES;
+  w.f.p = hot_base + t.w_f * WS_LANES;
+  w.iw.p = hot_base + t.w_iw * WS_LANES;
+  w.k.p = hot_base + t.w_k * WS_LANES;
+  w.g.p = hot_base + t.w_g * WS_LANES;
+  w.rr.p = hot_base + t.w_rr * WS_LANES;
+  w.dt.p = hot_base + t.w_dt * WS_LANES;
+  w.lu.p = hot_base + t.w_lu * WS_LANES;
+  w.tmp.p = cold_base + (t.w_tmp - t.hot_doubles) * WS_LANES;
+  w.f0.p = cold_base + (t.w_f0 - t.hot_doubles) * WS_LANES;
+  w.xh.p = cold_base + (t.w_xh - t.hot_doubles) * WS_LANES;
+  w.eh.p = cold_base + (t.w_eh - t.hot_doubles) * WS_LANES;
+  w.th.p = cold_base + (t.w_th - t.hot_doubles) * WS_LANES;
+  return w;
+}
 
 NB_HD __forceinline__ WS make_ws(const Net& t, double* lane_base) {
   WS w;
@@ -266,13 +291,32 @@ NB_HD inline void assemble_M(const Net& t, const WS& w, const LV& v,
   }
 }
 
+// Finite and nonzero, decided on the exponent bits with integer ops (FP64
+// compares would occupy the FP64 pipe).
+NB_HD __forceinline__ long long dbits(double v) {
+#ifdef __CUDA_ARCH__
+  return __double_as_longlong(v);
+#else
+  long long b;
+  memcpy(&b, &v, sizeof(b));
+  return b;
+#endif
+}
+NB_HD __forceinline__ bool finite_nonzero(double v) {
+  const long long b = dbits(v) & 0x7fffffffffffffffLL;
+  return b != 0 && b < 0x7ff0000000000000LL;
+}
+NB_HD __forceinline__ bool finite_bits(double v) {
+  return (dbits(v) & 0x7fffffffffffffffLL) < 0x7ff0000000000000LL;
+}
+
 // static-pivot LU in place; the diagonal keeps 1/pivot.  false if singular.
 NB_HD inline bool factor_M(const Net& t, const WS& w) {
   bool ok = true;
   for (int k = 0; k < t.n; ++k) {
     const Pivot p = t.piv[k];
     const double pv = w.lu[p.dslot];
-    ok = ok && (fabs(pv) > 0.0) && isfinite(pv);
+    ok = ok && finite_nonzero(pv);
     const double inv = 1.0 / pv;
     w.lu[p.dslot] = inv;
     const int nu = p.uend - p.ubeg;
@@ -446,8 +490,8 @@ NB_HD inline bool zone_init(const Net& t, Zone& s, const WS& w, const BurnParams
   eval_terms(t, w, x0);
   eval_f(t, w, x0, w.f0);
   s.c_rhs++;
-  for (int r = 0; r < t.R; ++r) fin = fin && isfinite(w.k[r]);
-  for (int i = 0; i < n; ++i) fin = fin && isfinite(w.f0[i]);
+  for (int r = 0; r < t.R; ++r) fin = fin && finite_bits(w.k[r]);
+  for (int i = 0; i < n; ++i) fin = fin && finite_bits(w.f0[i]);
   if (!fin) { s.status = NB_Z_NONFINITE; return true; }
   if (!(P.t_end > 0.0)) return true;
   // starting step: Hairer-Norsett-Wanner I, Sec. II.4, p = 1
@@ -555,7 +599,7 @@ NB_HD inline bool zone_attempt(const Net& t, Zone& s, const WS& w,
     for (int i = 0; i < n; ++i) w.x[i] += w.d[i];
     s.c_newton++;
     const double nrm = wnorm(t, w, w.d);
-    if (!isfinite(nrm)) { ok = false; break; }
+    if (!finite_bits(nrm)) { ok = false; break; }
     if (nrm <= 1e-3) { converged = true; break; }
     if (m > 0) {
       const double theta = nrm / nrm_prev;
@@ -621,7 +665,9 @@ NB_HD inline bool zone_attempt(const Net& t, Zone& s, const WS& w,
   if (s.nconsec >= s.k + 1) {
     const int k = s.k;
     int best_q = k;
-    double best = step_factor(order_estimate(t, s, w, k, h), k);
+    // E_k is the step's own error estimate: the same extrapolation through
+    // the same points at the same time, so the same bits
+    double best = step_factor(err, k);
     if (k > 1) {
       const double fq = step_factor(order_estimate(t, s, w, k - 1, h), k - 1);
       if (fq > best) { best = fq; best_q = k - 1; }

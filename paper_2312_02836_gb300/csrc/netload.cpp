@@ -327,12 +327,16 @@ int build_blob(const nb_topology* T, const double* coeffs,
   // per-lane workspace layout (doubles)
   int w = 0;
   auto take = [&](int cnt) { int o = w; w += cnt; return o; };
+  // arrays touched inside every Newton iteration first ("hot": they may be
+  // placed in shared memory), then the history and start-up arrays
   h.w_x = take(n); h.w_xp = take(n); h.w_psi = take(n); h.w_d = take(n);
-  h.w_f = take(n); h.w_iw = take(n); h.w_tmp = take(n); h.w_f0 = take(n);
-  h.w_xh = take(HMAX * n); h.w_eh = take(HMAX); h.w_th = take(HMAX);
+  h.w_f = take(n); h.w_iw = take(n);
   h.w_k = take(R); h.w_g = take(R); h.w_rr = take(R);
   h.w_dt = take(nd + R);   // [dterms | R_r g_r]
   h.w_lu = take(nnz);
+  h.hot_doubles = w;
+  h.w_tmp = take(n); h.w_f0 = take(n);
+  h.w_xh = take(HMAX * n); h.w_eh = take(HMAX); h.w_th = take(HMAX);
   h.lane_doubles = w;
 
   // algorithmic FP64 operation counts per event (an FMA counts 2 flops;

@@ -52,7 +52,7 @@ def _check(expect, got, rtol, scale=None):
     # two methods accumulate them in different orders
     scale = (np.abs(expect).max() if scale is None else scale) + 1e-300
     err = np.abs(got - expect)
-    bad = err > rtol * np.abs(expect) + 1e-9 * scale
+    bad = err > rtol * np.abs(expect) + 1e-8 * scale
     assert not bad.any(), (np.where(bad), got[bad][:4], expect[bad][:4])
 
 
