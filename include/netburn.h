@@ -37,6 +37,7 @@
 #ifndef NETBURN_H
 #define NETBURN_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -180,6 +181,34 @@ int nb_tape_steps(void* tape, const int32_t** steps);
 int nb_burn_adjoint(nb_net net, void* tape, int32_t K, const double* gY,
                     const double* gE, const double* gT9, double* d_ln_mult,
                     double* dY0, double* dT0, void* stream);
+
+/* Burn without any device allocation.  The paper has no counterpart: this is
+ * for callers that may not allocate device memory while they run the burn
+ * (a solver whose memory is reserved up front by its own pool, a time step
+ * run while another library owns the allocator, code that cannot afford the
+ * implicit synchronisation of cudaMalloc/cudaFree).  Same arguments and
+ * results as nb_burn_batch (same per-zone integration, bit for bit), without
+ * a tape; the caller passes every input and output.
+ *  - Scratch: the work-queue counter and the per-zone workspace live in one
+ *    array of NB_NOALLOC_SCRATCH_BYTES compiled into the library, which every
+ *    GPU that loads the library keeps until the process exits.  The number
+ *    of zones in flight is capped so that their workspace fits; any Z works.
+ *    NB_E_TOO_LARGE when not even one block of threads_per_block zones fits
+ *    (a network whose per-zone workspace exceeds the array).
+ *  - Set-up: the first call on each device looks up the array's device
+ *    address (cudaGetSymbolAddress) with that device current; make that
+ *    first call before any stream capture on the device.
+ *  - All calls share the one array: calls that can overlap on the GPU (on
+ *    different streams, or from several host threads) race and corrupt each
+ *    other's results.  Serialise them.  Each call zeroes the counter itself.
+ *  - ws_in_shared is ignored (the workspace is always the fixed array). */
+#define NB_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+int nb_burn_batch_noalloc(nb_net net, int64_t Z, const double* Y0,
+                          const double* T9_0, const double* rho, double t_end,
+                          double rtol, double atol, const double* ln_mult,
+                          int32_t ln_mult_per_zone, double* Y, double* T9,
+                          double* E, int32_t* counters, int32_t* status,
+                          const nb_options* opt, void* stream);
 
 /* FP64 pipe microbenchmark (a hardware measurement; the paper has no
  * counterpart).  Runs 8 independent DFMA chains per thread on

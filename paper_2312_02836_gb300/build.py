@@ -9,7 +9,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libnetburn.so")
-SOURCES = ["burn.cu", "adjoint.cu", "probe.cu", "netload.cpp"]
+SOURCES = ["burn.cu", "adjoint.cu", "noalloc.cu", "probe.cu", "netload.cpp"]
 HEADERS = ["blob.h", "device.cuh", "host.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
