@@ -210,6 +210,13 @@ int nb_burn_batch_noalloc(nb_net net, int64_t Z, const double* Y0,
                           double* E, int32_t* counters, int32_t* status,
                           const nb_options* opt, void* stream);
 
+/* The FP64 exp the rate evaluation uses (Tang's table-driven method, see
+ * the kernels' expf64.cuh), and optionally the CUDA library exp, on a device
+ * array x [n]: y_tang [n] (and y_lib [n] unless NULL).  A diagnostic for
+ * its error bound; the paper has no counterpart.  Asynchronous on stream. */
+int nb_exp_eval(const double* x, double* y_tang, double* y_lib, int64_t n,
+                void* stream);
+
 /* FP64 pipe microbenchmark (a hardware measurement; the paper has no
  * counterpart).  Runs 8 independent DFMA chains per thread on
  * blocks_per_sm x SMs blocks of 256 threads, with only `active_lanes` of

@@ -25,7 +25,7 @@ KERNEL_PLAIN = 1
 EXPORTS = ("nb_net_load", "nb_net_free", "nb_net_get_info", "nb_default_options",
            "nb_burn_batch", "nb_burn_batch_host", "nb_tape_alloc", "nb_tape_free",
            "nb_tape_steps", "nb_burn_adjoint", "nb_burn_batch_noalloc",
-           "nb_probe_fp64", "nb_strerror")
+           "nb_exp_eval", "nb_probe_fp64", "nb_strerror")
 
 
 class Topology(C.Structure):
@@ -80,6 +80,8 @@ def load(build_if_needed: bool = True):
         lib.nb_burn_batch_noalloc.argtypes = [P, I64, P, P, P, D, D, D, P, I32, P,
                                               P, P, P, P, P, P]
         lib.nb_burn_batch_noalloc.restype = C.c_int
+        lib.nb_exp_eval.argtypes = [P, P, P, I64, P]
+        lib.nb_exp_eval.restype = C.c_int
         lib.nb_probe_fp64.argtypes = [I32, I32, I32, P, P]
         lib.nb_probe_fp64.restype = C.c_int
         lib.nb_strerror.argtypes = [C.c_int]

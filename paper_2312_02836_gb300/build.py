@@ -10,7 +10,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libnetburn.so")
 SOURCES = ["burn.cu", "adjoint.cu", "noalloc.cu", "probe.cu", "netload.cpp"]
-HEADERS = ["blob.h", "device.cuh", "host.h"]
+HEADERS = ["blob.h", "device.cuh", "host.h", "expf64.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

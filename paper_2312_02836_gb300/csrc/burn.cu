@@ -34,7 +34,7 @@ using namespace nb;
 // SPLIT = true: the Newton-loop arrays ("hot") of every warp in shared memory
 // after the (optional) blob copy, the history in global memory.
 template <bool SPLIT>
-__global__ void __launch_bounds__(128) k_burn_persistent(BurnParams P) {
+__global__ void __launch_bounds__(128, 2) k_burn_persistent(BurnParams P) {
   extern __shared__ __align__(16) unsigned char sm[];
   const unsigned char* blob = P.blob;
   if (P.blob_in_smem) {
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(128) k_burn_persistent(BurnParams P) {
   }
 }
 
-__global__ void __launch_bounds__(128) k_burn_plain(BurnParams P) {
+__global__ void __launch_bounds__(128, 2) k_burn_plain(BurnParams P) {
   const Net t = make_net(P.blob);
   const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= P.Z) return;

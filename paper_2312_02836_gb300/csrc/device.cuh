@@ -15,6 +15,7 @@
 #include <string.h>
 
 #include "blob.h"
+#include "expf64.cuh"
 #include "../../include/netburn.h"
 
 #ifndef NB_HD
@@ -193,33 +194,36 @@ NB_HD inline void eval_rates(const Net& t, const Zone& s, const WS& w,
     d3 = (1.0 / 3.0) * it13 * it13;
     d5 = (5.0 / 3.0) * t23;
   }
+  // one warp per scheduler leaves FP64 latency exposed: two reactions per
+  // iteration and two partial sums per exponent give independent chains
+#pragma unroll 2
   for (int r = 0; r < t.R; ++r) {
     const double* a = t.coef + 7 * r;
-    double e = a[0];
-    e = fma(a[1], iT, e);
-    e = fma(a[2], it13, e);
-    e = fma(a[3], t13, e);
-    e = fma(a[4], T9, e);
-    e = fma(a[5], T53, e);
-    e = fma(a[6], lnT, e);
+    double e1 = fma(a[1], iT, a[0]);
+    double e2 = a[4] * T9;
+    e1 = fma(a[2], it13, e1);
+    e2 = fma(a[5], T53, e2);
+    e1 = fma(a[3], t13, e1);
+    e2 = fma(a[6], lnT, e2);
+    double e = e1 + e2;
     if (s.lnm) e += s.lnm[r];
     const int nr = t.nrho[r];
     const double rp = nr == 0 ? 1.0 : (nr == 1 ? s.rho : s.rho2);
-    w.k[r] = exp(e) * (rp * t.scale[r]);
+    w.k[r] = exp_tang(e) * (rp * t.scale[r]);
     if (with_g) {
-      double gg = a[4];
-      gg = fma(a[1], d1, gg);
-      gg = fma(a[2], d2, gg);
-      gg = fma(a[3], d3, gg);
-      gg = fma(a[5], d5, gg);
-      gg = fma(a[6], iT, gg);
-      w.g[r] = gg;
+      double g1 = fma(a[1], d1, a[4]);
+      double g2 = a[5] * d5;
+      g1 = fma(a[2], d2, g1);
+      g2 = fma(a[6], iT, g2);
+      g1 = fma(a[3], d3, g1);
+      w.g[r] = g1 + g2;
     }
   }
 }
 
 // R_r = k_r prod Y over reactant occurrences, for state v
 NB_HD inline void eval_terms(const Net& t, const WS& w, const LV& v) {
+#pragma unroll 4
   for (int r = 0; r < t.R; ++r) {
     const int16_t* ra = t.reac + 3 * r;
     const int m = t.nreac[r];
@@ -232,32 +236,54 @@ NB_HD inline void eval_terms(const Net& t, const WS& w, const LV& v) {
 }
 
 NB_HD __forceinline__ double heat_capacity(const Net& t, const LV& v) {
-  double sy = 0.0;
-  for (int i = 0; i < t.N; ++i) sy += v[i];
+  double s0 = 0.0, s1 = 0.0;
+  int i = 0;
+  for (; i + 1 < t.N; i += 2) {
+    s0 += v[i];
+    s1 += v[i + 1];
+  }
+  if (i < t.N) s0 += v[i];
   const double T9 = v[t.N];
-  return 1.5 * sy + 1e-3 * T9 * T9 * T9;
+  return 1.5 * (s0 + s1) + 1e-3 * T9 * T9 * T9;
 }
 
 NB_HD __forceinline__ double eval_edot(const Net& t, const WS& w) {
-  double ed = 0.0;
-  for (int r = 0; r < t.R; ++r) ed = fma(t.Q[r], w.rr[r], ed);
-  return ed;
+  double e0 = 0.0, e1 = 0.0;
+  int r = 0;
+  for (; r + 1 < t.R; r += 2) {
+    e0 = fma(t.Q[r], w.rr[r], e0);
+    e1 = fma(t.Q[r + 1], w.rr[r + 1], e1);
+  }
+  if (r < t.R) e0 = fma(t.Q[r], w.rr[r], e0);
+  return e0 + e1;
+}
+
+// sum_e c[e] * v[idx[e]] over [beg, end), two interleaved partial sums
+template <class TI>
+NB_HD __forceinline__ double gather2(const double* c, const TI* idx, int beg, int end,
+                                     const LV& v) {
+  double a0 = 0.0, a1 = 0.0;
+  int e = beg;
+  for (; e + 1 < end; e += 2) {
+    a0 = fma(c[e], v[idx[e]], a0);
+    a1 = fma(c[e + 1], v[idx[e + 1]], a1);
+  }
+  if (e < end) a0 = fma(c[e], v[idx[e]], a0);
+  return a0 + a1;
 }
 
 // out = f(v) given w.rr for v
 NB_HD inline void eval_f(const Net& t, const WS& w, const LV& v, const LV& out) {
-  for (int i = 0; i < t.N; ++i) {
-    double acc = 0.0;
-    for (int e = t.rhs_ptr[i]; e < t.rhs_ptr[i + 1]; ++e)
-      acc = fma(t.rhs_c[e], w.rr[t.rhs_r[e]], acc);
-    out[i] = acc;
-  }
+#pragma unroll 2
+  for (int i = 0; i < t.N; ++i)
+    out[i] = gather2(t.rhs_c, t.rhs_r, t.rhs_ptr[i], t.rhs_ptr[i + 1], w.rr);
   if (t.sh) out[t.N] = eval_edot(t, w) / heat_capacity(t, v);
 }
 
 // M = alpha0 I - h J(v) into w.lu (needs w.k, w.g (self-heating), w.rr at v)
 NB_HD inline void assemble_M(const Net& t, const WS& w, const LV& v,
                                   double alpha0, double h) {
+#pragma unroll 4
   for (int d = 0; d < t.nd; ++d) {
     const int16_t o0 = t.dt_o[2 * d], o1 = t.dt_o[2 * d + 1];
     double q = w.k[t.dt_r[d]] * t.dt_m[d];
@@ -278,10 +304,9 @@ NB_HD inline void assemble_M(const Net& t, const WS& w, const LV& v,
     b2 = -fT * (3e-3 * T9 * T9) * icv;
   }
   const double mh = -h;
+#pragma unroll 2
   for (int s = 0; s < t.nnz; ++s) {
-    double acc = 0.0;
-    for (int e = t.js_ptr[s]; e < t.js_ptr[s + 1]; ++e)
-      acc = fma(t.js_c[e], w.dt[t.js_src[e]], acc);
+    double acc = gather2(t.js_c, t.js_src, t.js_ptr[s], t.js_ptr[s + 1], w.dt);
     const uint8_t fl = t.js_flag[s];
     if (fl & SLOT_TROW) acc = fma(acc, a1, b1);
     else if (fl & SLOT_TT) acc = fma(acc, a1, b2);
@@ -326,6 +351,7 @@ NB_HD inline bool factor_M(const Net& t, const WS& w) {
       const double l = w.lu[ls] * inv;
       w.lu[ls] = l;
       const double ml = -l;
+#pragma unroll 4
       for (int u = 0; u < nu; ++u, ++dpos) {
         const int ds = t.dslot[dpos];
         w.lu[ds] = fma(ml, w.lu[t.uslot[p.ubeg + u]], w.lu[ds]);
@@ -341,21 +367,33 @@ NB_HD __forceinline__ void tri_solve(const TriRow* rows, const int16_t* es,
                                           const LV& v) {
   for (int q = 0; q < n; ++q) {
     const TriRow r = rows[q];
-    double acc = v[r.tgt];
-    for (int e = r.beg; e < r.end; ++e) acc = fma(-lu[es[e]], v[ec[e]], acc);
+    double a0 = v[r.tgt], a1 = 0.0;
+    int e = r.beg;
+    for (; e + 1 < r.end; e += 2) {
+      a0 = fma(-lu[es[e]], v[ec[e]], a0);
+      a1 = fma(-lu[es[e + 1]], v[ec[e + 1]], a1);
+    }
+    if (e < r.end) a0 = fma(-lu[es[e]], v[ec[e]], a0);
+    double acc = a0 + a1;
     if (r.dslot >= 0) acc *= lu[r.dslot];
     v[r.tgt] = acc;
   }
 }
 
-// ||v|| = sqrt(mean (v_i * iw_i)^2), summed in index order
+// ||v|| = sqrt(mean (v_i * iw_i)^2), two interleaved partial sums
 NB_HD __forceinline__ double wnorm(const Net& t, const WS& w, const LV& v) {
-  double s = 0.0;
-  for (int i = 0; i < t.n; ++i) {
-    const double q = v[i] * w.iw[i];
-    s = fma(q, q, s);
+  double s0 = 0.0, s1 = 0.0;
+  int i = 0;
+  for (; i + 1 < t.n; i += 2) {
+    const double q0 = v[i] * w.iw[i], q1 = v[i + 1] * w.iw[i + 1];
+    s0 = fma(q0, q0, s0);
+    s1 = fma(q1, q1, s1);
   }
-  return sqrt(s / t.n);
+  if (i < t.n) {
+    const double q = v[i] * w.iw[i];
+    s0 = fma(q, q, s0);
+  }
+  return sqrt((s0 + s1) / t.n);
 }
 
 // Lagrange weights at time tt of the q+1 newest history points starting at

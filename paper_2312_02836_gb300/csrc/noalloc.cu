@@ -52,7 +52,7 @@ int scratch_address(int dev, void** out) {
 
 // The persistent claim loop of the burn with the workspace in global memory,
 // taking the counter and workspace from the fixed scratch.
-__global__ void __launch_bounds__(128) k_burn_noalloc(BurnParams P) {
+__global__ void __launch_bounds__(128, 2) k_burn_noalloc(BurnParams P) {
   extern __shared__ __align__(16) unsigned char sm[];
   const unsigned char* blob = P.blob;
   if (P.blob_in_smem) {

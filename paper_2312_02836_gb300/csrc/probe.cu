@@ -5,6 +5,7 @@
 // slots (on GB300 they do not: the per-warp cost is the same).
 #include <cuda_runtime.h>
 
+#include "expf64.cuh"
 #include "../../include/netburn.h"
 
 namespace {
@@ -22,7 +23,23 @@ __global__ void __launch_bounds__(256) k_probe_dfma(double* out, int iters, int 
   out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
 }
 
+__global__ void k_exp_eval(const double* x, double* y_tang, double* y_lib, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  y_tang[i] = nb::exp_tang(x[i]);
+  if (y_lib) y_lib[i] = exp(x[i]);
+}
+
 }  // namespace
+
+extern "C" int nb_exp_eval(const double* x, double* y_tang, double* y_lib, int64_t n,
+                           void* stream) {
+  if (n < 0 || (n > 0 && (!x || !y_tang))) return NB_E_ARG;
+  if (n == 0) return NB_OK;
+  const int tpb = 256;
+  k_exp_eval<<<(unsigned)((n + tpb - 1) / tpb), tpb, 0, (cudaStream_t)stream>>>(x, y_tang, y_lib, n);
+  return cudaGetLastError() == cudaSuccess ? NB_OK : NB_E_CUDA;
+}
 
 extern "C" int nb_probe_fp64(int32_t active_lanes, int32_t iters, int32_t blocks_per_sm,
                              double* tflops_useful, double* ms_out) {

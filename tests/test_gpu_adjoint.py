@@ -47,12 +47,13 @@ def _gpu_adjoint(nb, torch, net, z, s, gY, gE, gT9, ln_mult=None, max_steps=2000
             fw.counters.cpu().numpy(), fw.Y.cpu().numpy(), fw.status.cpu().numpy())
 
 
-def _check(expect, got, rtol, scale=None):
-    # entries far below the gradient's scale come from cancelling sums; the
-    # two methods accumulate them in different orders
+def _check(expect, got, rtol, scale=None, out_mag=0.0):
+    # Entries far below the gradient's scale come from cancelling sums that
+    # the two methods accumulate in different orders; a gradient of an
+    # output O is known to ~1e-13 |O| absolute (rounding over ~10^3 steps).
     scale = (np.abs(expect).max() if scale is None else scale) + 1e-300
     err = np.abs(got - expect)
-    bad = err > rtol * np.abs(expect) + 1e-8 * scale
+    bad = err > rtol * np.abs(expect) + 1e-8 * scale + 1e-13 * out_mag
     assert not bad.any(), (np.where(bad), got[bad][:4], expect[bad][:4])
 
 
@@ -71,7 +72,7 @@ def test_adjoint_matches_forward_sensitivity(name, Z):
     for q in range(5):
         gY[q + 1, np.arange(Z), top[:, q]] = 1.0
     gT9 = np.zeros((K, Z)) if net.self_heating else None
-    dl, dY0, dT0, cnt, _, st = _gpu_adjoint(nb, torch, net, z, s, gY, gE, gT9)
+    dl, dY0, dT0, cnt, Yf, st = _gpu_adjoint(nb, torch, net, z, s, gY, gE, gT9)
     assert (st == 0).all()
     sens = _forward_sens(net, z, s, range(Z))
     same = 0
@@ -81,10 +82,11 @@ def test_adjoint_matches_forward_sensitivity(name, Z):
         same += 1
         for q in range(K):
             w = gY[q, i]
+            mag = np.abs(w) @ np.abs(Yf[i]) + abs(gE[q, i]) * abs(o["E"][i])
             exp_l = w @ dx[:net.N, :net.R] + gE[q, i] * dE[:net.R]
-            _check(exp_l, dl[q, i], 1e-7)
+            _check(exp_l, dl[q, i], 1e-7, out_mag=mag)
             exp_y0 = w @ dx[:net.N, net.R:net.R + net.N] + gE[q, i] * dE[net.R:net.R + net.N]
-            _check(exp_y0, dY0[q, i], 1e-7)
+            _check(exp_y0, dY0[q, i], 1e-7, out_mag=mag)
             col = net.R + net.N   # T9: initial state entry or parameter
             exp_t = w @ dx[:net.N, col] + gE[q, i] * dE[col]
             _check(np.array([exp_t]), np.array([dT0[q, i]]), 1e-7,
@@ -111,7 +113,7 @@ def test_adjoint_cotangent_sets_are_independent_and_linear():
     for k in range(3):
         lin = one[k][0] + 2 * two[k][0]
         # linear up to rounding of the transposed solves
-        np.testing.assert_allclose(summed[k][0], lin, rtol=1e-8,
+        np.testing.assert_allclose(summed[k][0], lin, rtol=1e-7,
                                    atol=1e-10 * np.abs(lin).max())
 
 
