@@ -53,6 +53,27 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def profiled_traffic(Z, launch):
+    """DRAM bytes per launch from the committed ncu summary, or None when the
+    kernel sources, the zone count or the launch shape differ from the
+    profiled ones."""
+    path = os.path.join(ROOT, "profiles", "k_burn_persistent_chain13_heat.md")
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    for line in open(path):
+        if ":" in line and not line.startswith(("|", "#", " ")):
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+    shape = "%d,%d,%d" % (launch.get("threads_per_block", 0) or 128,
+                          launch.get("blocks_per_sm", 0) or 1,
+                          max(launch.get("ws_in_shared", 0), 0))
+    if (kv.get("source_hash") == kernel_source_hash() and kv.get("zones") == str(Z)
+            and kv.get("launch") == shape and "dram_bytes_per_launch" in kv):
+        return int(kv["dram_bytes_per_launch"])
+    return None
+
+
 class Clocks:
     """nvidia-smi samples during the timed region."""
 
@@ -152,7 +173,9 @@ def run_native(args):
     net_spec, zall, s = gen.problem(WORKLOAD, Z * ws)
     if args.t_end is not None:
         s["t_end"] = args.t_end
-    z = {k: np.ascontiguousarray(v[rank * Z:(rank + 1) * Z]) for k, v in zall.items()}
+    from paper_2312_02836_gb300.parallel import max_over_ranks, shard
+    lo, hi = shard(Z * ws, ws, rank)           # weak scaling: Z zones per rank
+    z = {k: np.ascontiguousarray(v[lo:hi]) for k, v in zall.items()}
     netc = nb.Network(net_spec)
     info = netc.info()
     Y0 = torch.from_numpy(z["Y"]).to(dev)
@@ -200,12 +223,7 @@ def run_native(args):
     barrier()
     clk = clocks.stop() if clocks else None
     ms = [a.elapsed_time(b) for a, b in ev]
-    mean_ms = statistics.mean(ms)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([mean_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        mean_ms = float(t.item())
+    mean_ms = max_over_ranks(statistics.mean(ms), dev)
     counters = out.counters.cpu().numpy()
     status = out.status.cpu().numpy()
     ops = metrics.burn_ops(info, counters, net_spec.self_heating)
@@ -250,12 +268,7 @@ def run_native(args):
     # ---- roofline of the burn kernel (one launch per step)
     achieved = ops["flops"] / (mean_ms * 1e-3) / 1e12
     peak = metrics.FP64_PEAK_TFLOPS
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "burn_traffic.json")
-    if os.path.exists(tpath):
-        tj = json.load(open(tpath))
-        if tj.get("source_hash") == kernel_source_hash() and tj.get("zones") == Z:
-            traffic = tj.get("dram_bytes_per_launch")
+    traffic = profiled_traffic(Z, launch)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "kernel": "k_burn_persistent",

@@ -60,6 +60,8 @@ extern "C" {
 #define NB_Z_NEWTON_FAIL 3   /* 10 consecutive Newton failures */
 #define NB_Z_TAPE_FULL 4     /* adjoint tape capacity exceeded */
 #define NB_Z_NONFINITE 5     /* non-finite input, rate or first derivative */
+#define NB_Z_TIMEOUT 6       /* the call's time budget ran out before the zone
+                                finished (outputs: the state reached) */
 
 /* per-zone counters, counters[z * NB_NCOUNT + c] */
 #define NB_NCOUNT 8
@@ -112,13 +114,30 @@ typedef struct {
 typedef struct {
   int32_t max_attempts;     /* step attempts per zone (default 500000) */
   int32_t kernel;           /* NB_KERNEL_* */
-  int32_t threads_per_block;/* 0 = library choice */
+  int32_t threads_per_block;/* 0 = 128; a multiple of 32, at most 256
+                               (128 for the plain kernel) */
   int32_t blocks_per_sm;    /* 0 = library choice (persistent kernel) */
   int32_t blob_in_shared;   /* -1 auto, 0 global (L1), 1 shared memory */
-  int32_t ws_in_shared;     /* persistent kernel: -1 auto, 0 per-zone work
-                               arrays in global memory, 1 the Newton-loop
-                               arrays in shared memory (history stays global) */
-  int32_t reserved[2];
+  int32_t ws_in_shared;     /* persistent kernel: the first ws_in_shared warps
+                               of each block keep their Newton-loop arrays in
+                               shared memory (history stays in global
+                               memory); <= 0: all work arrays in the global
+                               workspace (the default) */
+  int32_t schedule;         /* persistent kernel claim order: 0 zone index
+                               order; 1 longest first (default): a pre-pass
+                               computes every zone's starting step h0 (the
+                               integrator's own start-up) and zones are
+                               claimed in increasing h0, which tracks their
+                               step count, so the last zones claimed are
+                               short and a warp's lanes get alike zones */
+  int32_t reserved;
+  double time_budget_s;     /* > 0: device watchdog.  Every lane reads the GPU
+                               timer between step attempts; once the budget,
+                               counted from the start of its block, has run
+                               out it ends its zone with NB_Z_TIMEOUT and
+                               ends every zone it claims after that the same
+                               way, so the call always finishes.  0: none.
+                               Ignored by nb_burn_batch_noalloc. */
 } nb_options;
 
 #define NB_KERNEL_PERSISTENT 0  /* lane-per-zone, device work queue */

@@ -20,7 +20,7 @@ from . import _abi
 from ._abi import (COUNTER_NAMES, KERNEL_PERSISTENT, KERNEL_PLAIN, NCOUNT,
                    ZONE_STATUS, NetburnError)
 
-__all__ = ["Network", "burn", "burn_host", "Tape", "adjoint", "Burn",
+__all__ = ["Network", "burn", "burn_host", "BurnGraph", "Tape", "adjoint", "Burn",
            "BurnResult", "NetburnError", "COUNTER_NAMES", "ZONE_STATUS",
            "KERNEL_PERSISTENT", "KERNEL_PLAIN", "library_path", "probe_fp64"]
 
@@ -103,7 +103,7 @@ class BurnResult(NamedTuple):
 
 
 def _options(kernel, threads_per_block, blocks_per_sm, blob_in_shared,
-             max_attempts, ws_in_shared=-1):
+             max_attempts, ws_in_shared=-1, time_budget_s=0.0, schedule=None):
     o = _abi.Options()
     _abi.load().nb_default_options(C.byref(o))
     if isinstance(kernel, str):
@@ -114,6 +114,9 @@ def _options(kernel, threads_per_block, blocks_per_sm, blob_in_shared,
     o.blob_in_shared = int(blob_in_shared)
     o.max_attempts = int(max_attempts)
     o.ws_in_shared = int(ws_in_shared)
+    o.time_budget_s = float(time_budget_s)
+    if schedule is not None:
+        o.schedule = {"fifo": 0, "longest_first": 1}.get(schedule, schedule)
     return o
 
 
@@ -132,8 +135,8 @@ def _dev(t, torch, name, shape=None):
 def burn(net: Network, Y0, T9, rho, t_end: float, rtol: float, atol: float,
          ln_mult=None, *, kernel="persistent", tape: "Optional[Tape]" = None,
          threads_per_block=0, blocks_per_sm=0, blob_in_shared=-1,
-         ws_in_shared=-1, max_attempts=500000, stream=None,
-         out: Optional[BurnResult] = None):
+         ws_in_shared=-1, max_attempts=500000, time_budget_s=0.0, schedule=None,
+         stream=None, out: Optional[BurnResult] = None):
     """Burn Z zones on the GPU.  Y0 [Z,N], T9 [Z], rho [Z] CUDA float64;
     ln_mult None, [R] or [Z,R].  Returns BurnResult of CUDA tensors."""
     torch = _torch()
@@ -158,7 +161,7 @@ def burn(net: Network, Y0, T9, rho, t_end: float, rtol: float, atol: float,
                          torch.empty((Z, NCOUNT), dtype=torch.int32, device=dev),
                          torch.empty((Z,), dtype=torch.int32, device=dev))
     o = _options(kernel, threads_per_block, blocks_per_sm, blob_in_shared,
-                 max_attempts, ws_in_shared)
+                 max_attempts, ws_in_shared, time_budget_s, schedule)
     st = stream if stream is not None else torch.cuda.current_stream(dev)
     lib = _abi.load()
     ptr = lambda t: None if t is None else t.data_ptr()
@@ -172,6 +175,32 @@ def burn(net: Network, Y0, T9, rho, t_end: float, rtol: float, atol: float,
     if tape is not None:
         tape._recorded(Z, ln_mult, float(t_end), float(rtol), float(atol))
     return out
+
+
+class BurnGraph:
+    """A burn captured once in a CUDA graph and replayed.
+
+    The tensors passed here are the graph's inputs: write new zone data into
+    them in place (same shapes) and call ``replay()``; ``out`` holds the
+    results.  Capture happens after one ordinary burn with the same launch
+    options, so the device workspace is already allocated and the captured
+    work is one counter reset and one kernel launch."""
+
+    def __init__(self, net: "Network", Y0, T9, rho, t_end, rtol, atol,
+                 ln_mult=None, **launch):
+        torch = _torch()
+        self.args = (net, Y0, T9, rho, t_end, rtol, atol, ln_mult)
+        self.launch = launch
+        self.out = burn(*self.args, **launch)
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            burn(*self.args, out=self.out, **launch)
+        torch.cuda.synchronize()
+
+    def replay(self) -> "BurnResult":
+        self.graph.replay()
+        return self.out
 
 
 def burn_host(net: Network, Y0, T9, rho, t_end, rtol, atol, ln_mult=None, *,

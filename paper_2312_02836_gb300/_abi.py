@@ -14,7 +14,7 @@ NB_OK = 0
 ERRORS = {-1: "NB_E_ARG", -2: "NB_E_TOPOLOGY", -3: "NB_E_TOO_LARGE",
           -4: "NB_E_CUDA", -5: "NB_E_NOMEM", -6: "NB_E_TAPE"}
 ZONE_STATUS = {0: "OK", 1: "MAX_STEPS", 2: "DT_UNDERFLOW", 3: "NEWTON_FAIL",
-               4: "TAPE_FULL", 5: "NONFINITE"}
+               4: "TAPE_FULL", 5: "NONFINITE", 6: "TIMEOUT"}
 NCOUNT = 8
 COUNTER_NAMES = ("accepted", "rejected_error", "rejected_newton", "newton_iters",
                  "jacobians", "rhs_evals", "rate_evals", "edot_evals")
@@ -52,7 +52,8 @@ class Options(C.Structure):
     _fields_ = [("max_attempts", C.c_int32), ("kernel", C.c_int32),
                 ("threads_per_block", C.c_int32), ("blocks_per_sm", C.c_int32),
                 ("blob_in_shared", C.c_int32), ("ws_in_shared", C.c_int32),
-                ("reserved", C.c_int32 * 2)]
+                ("schedule", C.c_int32), ("reserved", C.c_int32),
+                ("time_budget_s", C.c_double)]
 
 
 def load(build_if_needed: bool = True):

@@ -3,8 +3,10 @@
 The kernel maps one zone to one lane, so the tunables are how many zones are
 in flight per SM and where their work arrays live:
 
-* ``ws_in_shared`` 1: the Newton-loop arrays of every warp in shared memory
-  (history in global memory); 0: everything in the global workspace;
+* ``ws_in_shared`` w: the first w warps of each block keep their Newton-loop
+  arrays in shared memory (history in global memory), the others keep
+  everything in the global workspace, which stays L2-resident only while
+  few lanes are in flight;
 * ``threads_per_block`` and ``blocks_per_sm``: zones in flight.  Fewer lanes
   than zones let the device queue refill lanes whose zone finished; more
   lanes hide more latency but grow the workspace beyond L2.
@@ -20,13 +22,14 @@ from typing import Optional
 _CACHE: dict = {}
 
 DEFAULT_CANDIDATES = (
-    dict(ws_in_shared=1, threads_per_block=32, blocks_per_sm=3),
-    dict(ws_in_shared=1, threads_per_block=32, blocks_per_sm=2),
-    dict(ws_in_shared=1, threads_per_block=64, blocks_per_sm=1),
     dict(ws_in_shared=0, threads_per_block=128, blocks_per_sm=1),
+    dict(ws_in_shared=1, threads_per_block=160, blocks_per_sm=1),
+    dict(ws_in_shared=2, threads_per_block=192, blocks_per_sm=1),
+    dict(ws_in_shared=3, threads_per_block=224, blocks_per_sm=1),
+    dict(ws_in_shared=3, threads_per_block=256, blocks_per_sm=1),
+    dict(ws_in_shared=3, threads_per_block=96, blocks_per_sm=1),
     dict(ws_in_shared=0, threads_per_block=64, blocks_per_sm=2),
     dict(ws_in_shared=0, threads_per_block=128, blocks_per_sm=2),
-    dict(ws_in_shared=0, threads_per_block=64, blocks_per_sm=3),
 )
 
 

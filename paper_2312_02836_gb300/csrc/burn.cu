@@ -8,6 +8,7 @@
 //  * plain: one thread per zone, one launch over all zones (the comparison
 //    launch).
 #include <cuda_runtime.h>
+#include <cub/device/device_radix_sort.cuh>
 
 #include <algorithm>
 #include <cmath>
@@ -30,11 +31,12 @@ using namespace nb;
 
 // ------------------------------------------------------------------ kernels
 
-// SPLIT = false: the whole per-lane workspace in global memory.
-// SPLIT = true: the Newton-loop arrays ("hot") of every warp in shared memory
-// after the (optional) blob copy, the history in global memory.
-template <bool SPLIT>
-__global__ void __launch_bounds__(128, 2) k_burn_persistent(BurnParams P) {
+// Work arrays of a lane: the first P.smem_warps warps of every block keep
+// their Newton-loop ("hot") arrays in shared memory after the (optional) blob
+// copy and only their history in global memory; the other warps keep
+// everything in the global workspace.  Per block the global workspace holds
+// smem_warps x cold + (warps - smem_warps) x lane_doubles doubles per lane.
+__global__ void __launch_bounds__(256, 1) k_burn_persistent(BurnParams P) {
   extern __shared__ __align__(16) unsigned char sm[];
   const unsigned char* blob = P.blob;
   if (P.blob_in_smem) {
@@ -46,19 +48,25 @@ __global__ void __launch_bounds__(128, 2) k_burn_persistent(BurnParams P) {
   }
   const Net t = make_net(blob);
   const int lane = threadIdx.x & 31;
-  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int wib = threadIdx.x >> 5;
+  const int wpb = blockDim.x >> 5;
+  const long long cold = t.lane_doubles - t.hot_doubles;
+  const long long block_doubles =
+      ((long long)P.smem_warps * cold + (long long)(wpb - P.smem_warps) * t.lane_doubles) * WS_LANES;
+  double* gbase = P.ws + (long long)blockIdx.x * block_doubles;
   WS w;
-  if (SPLIT) {
+  if (wib < P.smem_warps) {
     double* hot = reinterpret_cast<double*>(sm + (P.blob_in_smem ? P.blob_bytes : 0)) +
-                  (size_t)(threadIdx.x >> 5) * t.hot_doubles * WS_LANES + lane;
-    double* cold = P.ws + warp * (long long)(t.lane_doubles - t.hot_doubles) * WS_LANES + lane;
-    w = make_ws_split(t, hot, cold);
+                  (size_t)wib * t.hot_doubles * WS_LANES + lane;
+    w = make_ws_split(t, hot, gbase + (long long)wib * cold * WS_LANES + lane);
   } else {
-    w = make_ws(t, P.ws + warp * (long long)t.lane_doubles * WS_LANES + lane);
+    w = make_ws(t, gbase + (long long)P.smem_warps * cold * WS_LANES +
+                       (long long)(wib - P.smem_warps) * t.lane_doubles * WS_LANES + lane);
   }
   Zone s;
   s.z = -1;
   bool active = false, retired = false, fresh = false;
+  const unsigned long long t_start = P.budget_ns ? gpu_ns() : 0ull;
   for (;;) {
     const unsigned need = __ballot_sync(0xffffffffu, !active && !retired);
     if (need) {
@@ -69,7 +77,7 @@ __global__ void __launch_bounds__(128, 2) k_burn_persistent(BurnParams P) {
       if (!active && !retired) {
         const unsigned long long z = base + __popc(need & ((1u << lane) - 1u));
         if (z < (unsigned long long)P.Z) {
-          s.z = (long long)z;
+          s.z = P.order ? (long long)P.order[z] : (long long)z;
           active = true;
           fresh = true;
         } else {
@@ -79,8 +87,18 @@ __global__ void __launch_bounds__(128, 2) k_burn_persistent(BurnParams P) {
     }
     if (__all_sync(0xffffffffu, retired)) break;
     if (active) {
+      const bool expired = P.budget_ns && gpu_ns() - t_start > P.budget_ns;
       bool done;
-      if (fresh) {
+      if (expired && fresh) {
+        zone_timeout_unstarted(t, s.z, P);
+        fresh = false;
+        active = false;
+        continue;
+      }
+      if (expired) {
+        s.status = NB_Z_TIMEOUT;
+        done = true;
+      } else if (fresh) {
         done = zone_init(t, s, w, P);
         fresh = false;
       } else {
@@ -94,6 +112,25 @@ __global__ void __launch_bounds__(128, 2) k_burn_persistent(BurnParams P) {
   }
 }
 
+// Scheduling pre-pass: each zone's starting step h0 (the integrator's own
+// start-up, nothing recorded) as its sort key; zones that finish in start-up
+// go last.
+__global__ void __launch_bounds__(128, 2) k_burn_estimate(BurnParams P, double* key,
+                                                           int32_t* idx) {
+  const Net t = make_net(P.blob);
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const WS w = make_ws(t, P.ws + warp * (long long)t.lane_doubles * WS_LANES + lane);
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x; z < P.Z; z += stride) {
+    Zone s;
+    s.z = z;
+    const bool done = zone_init(t, s, w, P);
+    key[z] = done ? 1e300 : s.h;
+    idx[z] = (int32_t)z;
+  }
+}
+
 __global__ void __launch_bounds__(128, 2) k_burn_plain(BurnParams P) {
   const Net t = make_net(P.blob);
   const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -103,8 +140,19 @@ __global__ void __launch_bounds__(128, 2) k_burn_plain(BurnParams P) {
   const WS w = make_ws(t, lane_base);
   Zone s;
   s.z = gid;
+  const unsigned long long t_start = P.budget_ns ? gpu_ns() : 0ull;
+  if (P.budget_ns && gpu_ns() - t_start > P.budget_ns) {
+    zone_timeout_unstarted(t, gid, P);
+    return;
+  }
   bool done = zone_init(t, s, w, P);
-  while (!done) done = zone_attempt(t, s, w, P);
+  while (!done) {
+    if (P.budget_ns && gpu_ns() - t_start > P.budget_ns) {
+      s.status = NB_Z_TIMEOUT;
+      break;
+    }
+    done = zone_attempt(t, s, w, P);
+  }
   zone_finish(t, s, w, P);
 }
 
@@ -122,6 +170,7 @@ void nb_default_options(nb_options* o) {
   o->threads_per_block = 0;
   o->blocks_per_sm = 0;
   o->blob_in_shared = -1;
+  o->schedule = 1;
 }
 
 const char* nb_strerror(int code) {
@@ -184,6 +233,8 @@ int nb_net_free(nb_net net) {
   cudaFree(net->queue);
   if (net->ws) cudaFree(net->ws);
   if (net->stage) cudaFree(net->stage);
+  if (net->ws_adj) cudaFree(net->ws_adj);
+  if (net->sched) cudaFree(net->sched);
   delete net;
   return NB_OK;
 }
@@ -215,14 +266,43 @@ int nb_net_get_info(nb_net net, nb_net_info* o) {
 
 }  // extern "C"
 
+// Longest-first claim order: h0 of every zone (pre-pass over the workspace
+// lanes already allocated), then a radix sort of (h0, zone).  Sets P.order.
+static int schedule_longest_first(nb_net net, BurnParams& P, long long lanes,
+                                  cudaStream_t st) {
+  const long long Z = P.Z;
+  if (Z > 0x7fffffffLL) return NB_E_TOO_LARGE;
+  size_t temp = 0;
+  CK(cub::DeviceRadixSort::SortPairs(nullptr, temp, (const double*)nullptr, (double*)nullptr,
+                                     (const int32_t*)nullptr, (int32_t*)nullptr, (int)Z, 0,
+                                     64, st));
+  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  const size_t kb = al((size_t)Z * 8), ib = al((size_t)Z * 4);
+  const size_t need = 2 * kb + 2 * ib + al(temp);
+  int rc = nb::ensure((void**)&net->sched, &net->sched_bytes, need);
+  if (rc) return rc;
+  unsigned char* base = net->sched;
+  double* k_in = (double*)base;
+  double* k_out = (double*)(base + kb);
+  int32_t* i_in = (int32_t*)(base + 2 * kb);
+  int32_t* i_out = (int32_t*)(base + 2 * kb + ib);
+  void* tmp = base + 2 * kb + 2 * ib;
+  BurnParams E = P;
+  E.use_tape = 0;
+  const long long fit = (long long)(net->ws_bytes / ((size_t)net->h.lane_doubles * sizeof(double)));
+  const long long eblocks = std::max(1LL, std::min(lanes, fit) / 128);
+  k_burn_estimate<<<(unsigned)eblocks, 128, 0, st>>>(E, k_in, i_in);
+  CK(cudaGetLastError());
+  CK(cub::DeviceRadixSort::SortPairs(tmp, temp, k_in, k_out, i_in, i_out, (int)Z, 0, 64, st));
+  P.order = i_out;
+  return NB_OK;
+}
+
 // Launch one burn (device pointers).  Caller holds net->mu.
 static int launch_burn(nb_net net, BurnParams& P, const nb_options& o,
                        cudaStream_t st) {
-  const size_t hot_warp0 = (size_t)net->h.hot_doubles * WS_LANES * sizeof(double);
-  const bool split0 = o.kernel != NB_KERNEL_PLAIN &&
-                      (o.ws_in_shared > 0 || (o.ws_in_shared < 0 && hot_warp0 <= 64 * 1024));
-  const int tpb = o.threads_per_block > 0 ? o.threads_per_block : (split0 ? 32 : 128);
-  if (tpb % 32 != 0 || tpb > 128) return NB_E_ARG;
+  const int tpb = o.threads_per_block > 0 ? o.threads_per_block : 128;
+  if (tpb % 32 != 0 || tpb > 256 || (o.kernel == NB_KERNEL_PLAIN && tpb > 128)) return NB_E_ARG;
   const size_t lane_bytes = (size_t)net->h.lane_doubles * sizeof(double);
   P.blob = net->d_blob;
   P.blob_bytes = net->h.bytes;
@@ -237,37 +317,44 @@ static int launch_burn(nb_net net, BurnParams& P, const nb_options& o,
     CK(cudaGetLastError());
     return NB_OK;
   }
-  int in_smem = o.blob_in_shared;
   const size_t blob_b = (size_t)net->h.bytes;
   const size_t hot_warp = (size_t)net->h.hot_doubles * WS_LANES * sizeof(double);
-  int split = o.ws_in_shared;
-  if (split < 0) split = hot_warp <= 64 * 1024 ? 1 : 0;
-  if (in_smem < 0) in_smem = blob_b <= 96 * 1024 && (!split || blob_b + hot_warp <= 160 * 1024);
-  size_t dyn = in_smem ? blob_b : 0;
-  if (split) dyn += (size_t)(tpb / 32) * hot_warp;
+  const int wpb = tpb / 32;
+  // ws_in_shared: -1 none by default, >= 1 that many warps of each block
+  // keep their Newton-loop arrays in shared memory
+  const int smem_warps = o.ws_in_shared > 0 ? std::min(o.ws_in_shared, wpb) : 0;
+  int in_smem = o.blob_in_shared;
+  if (in_smem < 0) in_smem = blob_b <= 96 * 1024 && blob_b + smem_warps * hot_warp <= net->smem_optin;
+  size_t dyn = (in_smem ? blob_b : 0) + (size_t)smem_warps * hot_warp;
   if (dyn > net->smem_optin) return NB_E_TOO_LARGE;
-  auto kfun = split ? k_burn_persistent<true> : k_burn_persistent<false>;
   if (dyn > 48 * 1024)
-    CK(cudaFuncSetAttribute(kfun, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    CK(cudaFuncSetAttribute(k_burn_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
   int bps = o.blocks_per_sm;
   int occ = 0;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfun, tpb, dyn));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_burn_persistent, tpb, dyn));
   if (occ < 1) return NB_E_TOO_LARGE;
-  if (bps <= 0) bps = std::min(occ, 512 / tpb);
+  if (bps <= 0) bps = 1;
   bps = std::max(1, std::min(bps, occ));
   long long blocks = (long long)bps * net->sm_count;
   const long long needed_blocks = (P.Z + tpb - 1) / tpb;
   if (blocks > needed_blocks) blocks = needed_blocks;
-  const size_t per_lane = split ? lane_bytes - (size_t)net->h.hot_doubles * sizeof(double)
-                                : lane_bytes;
-  const size_t need = std::max<size_t>((size_t)blocks * tpb * per_lane, 256);
+  const size_t cold_bytes = lane_bytes - (size_t)net->h.hot_doubles * sizeof(double);
+  const size_t per_block = (size_t)32 * (smem_warps * cold_bytes + (wpb - smem_warps) * lane_bytes);
+  size_t need = std::max<size_t>((size_t)blocks * per_block, 256);
+  if (o.schedule == 1) need = std::max(need, (size_t)128 * lane_bytes);  // pre-pass lanes
   int rc = nb::ensure((void**)&net->ws, &net->ws_bytes, need);
   if (rc) return rc;
   P.ws = net->ws;
   P.queue = net->queue;
   P.blob_in_smem = in_smem;
+  P.smem_warps = smem_warps;
+  P.order = nullptr;
+  if (o.schedule == 1 && P.Z > 1) {
+    rc = schedule_longest_first(net, P, blocks * (long long)tpb, st);
+    if (rc) return rc;
+  }
   CK(cudaMemsetAsync(net->queue, 0, sizeof(unsigned long long), st));
-  kfun<<<(unsigned)blocks, tpb, dyn, st>>>(P);
+  k_burn_persistent<<<(unsigned)blocks, tpb, dyn, st>>>(P);
   CK(cudaGetLastError());
   return NB_OK;
 }
@@ -300,6 +387,8 @@ extern "C" int nb_burn_batch(nb_net net, int64_t Z, const double* Y0, const doub
   P.lnm = ln_mult; P.lnm_per_zone = ln_mult_per_zone ? 1 : 0;
   P.Y = Y; P.T9 = T9; P.E = E; P.counters = counters; P.status = status;
   P.max_attempts = o.max_attempts;
+  if (!(o.time_budget_s >= 0.0)) return NB_E_ARG;
+  P.budget_ns = o.time_budget_s > 0.0 ? (unsigned long long)(o.time_budget_s * 1e9) + 1ull : 0ull;
   cudaStream_t st = (cudaStream_t)stream;
   std::lock_guard<std::mutex> lk(net->mu);
   if (tape) {
@@ -367,6 +456,8 @@ extern "C" int nb_burn_batch_host(nb_net net, int64_t Z, const double* Y0,
   P.counters = (int32_t*)(b + off_c);
   P.status = (int32_t*)(b + off_s);
   P.max_attempts = o.max_attempts;
+  if (!(o.time_budget_s >= 0.0)) return NB_E_ARG;
+  P.budget_ns = o.time_budget_s > 0.0 ? (unsigned long long)(o.time_budget_s * 1e9) + 1ull : 0ull;
   rc = launch_burn(net, P, o, st);
   if (rc) return rc;
   CK(cudaMemcpyAsync(Y, b + off_Y, zN, cudaMemcpyDeviceToHost, st));

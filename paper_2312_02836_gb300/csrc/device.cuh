@@ -34,6 +34,7 @@ struct LV {
 
 struct Net {
   int n, N, R, sh, hasE, nnz, nd;
+  double inv_n;
   const double *coef, *Q, *scale, *rhs_c, *dt_m, *js_c, *rg_c;
   const int32_t *nrho, *nreac, *rhs_ptr, *js_ptr, *diag_orig, *rg_ptr;
   const int16_t *reac, *rhs_r, *dt_r, *dt_o, *dt_j, *js_src, *lslot, *uslot, *dslot;
@@ -55,6 +56,7 @@ NB_HD inline Net make_net(const unsigned char* b) {
   Net t;
   t.n = h->n; t.N = h->N; t.R = h->R; t.sh = h->self_heating; t.hasE = h->has_E;
   t.nnz = h->nnz; t.nd = h->nd;
+  t.inv_n = 1.0 / h->n;
   t.coef = at<double>(b, h->o_coef); t.Q = at<double>(b, h->o_Q);
   t.scale = at<double>(b, h->o_scale); t.rhs_c = at<double>(b, h->o_rhs_c);
   t.dt_m = at<double>(b, h->o_dt_m); t.js_c = at<double>(b, h->o_js_c);
@@ -160,6 +162,9 @@ struct BurnParams {
   unsigned long long* queue;  // zone counter of the persistent kernel
   TapeDev tape;
   int use_tape;
+  int smem_warps;             // warps per block with hot arrays in shared memory
+  unsigned long long budget_ns;  // watchdog budget per block, 0 = none
+  const int32_t* order;       // claim order (zone index per claim), or null
 };
 
 // Register state of the zone a lane is integrating.
@@ -182,9 +187,9 @@ NB_HD __forceinline__ int hslot(const Zone& s, int j) {
 NB_HD inline void eval_rates(const Net& t, const Zone& s, const WS& w,
                                   double T9, bool with_g) {
   const double t13 = cbrt(T9);
-  const double it13 = 1.0 / t13;
   const double iT = 1.0 / T9;
   const double t23 = t13 * t13;
+  const double it13 = t23 * iT;          // T9^(-1/3) without a second division
   const double T53 = T9 * t23;
   const double lnT = log(T9);
   double d1 = 0.0, d2 = 0.0, d3 = 0.0, d5 = 0.0;
@@ -380,8 +385,9 @@ NB_HD __forceinline__ void tri_solve(const TriRow* rows, const int16_t* es,
   }
 }
 
-// ||v|| = sqrt(mean (v_i * iw_i)^2), two interleaved partial sums
-NB_HD __forceinline__ double wnorm(const Net& t, const WS& w, const LV& v) {
+// ||v||^2 = mean (v_i * iw_i)^2, two interleaved partial sums (the tests
+// compare squares, which spares a square root per norm)
+NB_HD __forceinline__ double wnorm2(const Net& t, const WS& w, const LV& v) {
   double s0 = 0.0, s1 = 0.0;
   int i = 0;
   for (; i + 1 < t.n; i += 2) {
@@ -393,7 +399,7 @@ NB_HD __forceinline__ double wnorm(const Net& t, const WS& w, const LV& v) {
     const double q = v[i] * w.iw[i];
     s0 = fma(q, q, s0);
   }
-  return sqrt((s0 + s1) / t.n);
+  return (s0 + s1) * t.inv_n;
 }
 
 // Lagrange weights at time tt of the q+1 newest history points starting at
@@ -434,12 +440,13 @@ NB_HD inline void extrapolate(const Net& t, const Zone& s, const WS& w, int j0,
   }
 }
 
-NB_HD __forceinline__ double step_factor(double E, int q) {
-  if (!(E > 0.0)) return 5.0;
-  return 0.9 * pow(E, -1.0 / (q + 1));
+// 0.9 E^(-1/(q+1)) from E^2
+NB_HD __forceinline__ double step_factor(double E2, int q) {
+  if (!(E2 > 0.0)) return 5.0;
+  return 0.9 * pow(E2, -0.5 / (q + 1));
 }
 
-// E_q after acceptance: newest point vs extrapolation through the q+1 older
+// E_q^2 after acceptance: newest point vs extrapolation through the q+1 older
 NB_HD inline double order_estimate(const Net& t, const Zone& s, const WS& w,
                                         int q, double h) {
   extrapolate(t, s, w, 1, q, w.th[hslot(s, 0)], w.tmp);
@@ -450,7 +457,7 @@ NB_HD inline double order_estimate(const Net& t, const Zone& s, const WS& w,
     const double v = c * (w.xh[b0 + i] - w.tmp[i]) * w.iw[i];
     acc = fma(v, v, acc);
   }
-  return sqrt(acc / t.n);
+  return acc * t.inv_n;   // E_q^2
 }
 
 // Record an accepted point (time, step, state, energy, order); false when
@@ -636,15 +643,15 @@ NB_HD inline bool zone_attempt(const Net& t, Zone& s, const WS& w,
     tri_solve(t.bw, t.bw_s, t.bw_c, n, w.lu, w.d);
     for (int i = 0; i < n; ++i) w.x[i] += w.d[i];
     s.c_newton++;
-    const double nrm = wnorm(t, w, w.d);
-    if (!finite_bits(nrm)) { ok = false; break; }
-    if (nrm <= 1e-3) { converged = true; break; }
+    const double nrm2 = wnorm2(t, w, w.d);
+    if (!finite_bits(nrm2)) { ok = false; break; }
+    if (nrm2 <= 1e-6) { converged = true; break; }          // ||d|| <= 1e-3
     if (m > 0) {
-      const double theta = nrm / nrm_prev;
-      if (theta > 0.9) { ok = false; break; }
-      if (theta / (1.0 - theta) * nrm <= 1e-3) { converged = true; break; }
+      if (nrm2 > 0.81 * nrm_prev) { ok = false; break; }     // theta > 0.9
+      const double theta = sqrt(nrm2 / nrm_prev);
+      if (theta / (1.0 - theta) * sqrt(nrm2) <= 1e-3) { converged = true; break; }
     }
-    nrm_prev = nrm;
+    nrm_prev = nrm2;
   }
   if (!converged) {
     s.c_rej_newton++;
@@ -655,18 +662,18 @@ NB_HD inline bool zone_attempt(const Net& t, Zone& s, const WS& w,
   s.nfail = 0;
   // local error estimate
   const double c = s.nh >= kk + 1 ? h / (t_new - w.th[hslot(s, kk)]) : 0.5;
-  double err;
+  double err2;   // err^2
   {
     double acc = 0.0;
     for (int i = 0; i < n; ++i) {
       const double v = c * (w.x[i] - w.xp[i]) * w.iw[i];
       acc = fma(v, v, acc);
     }
-    err = sqrt(acc / n);
+    err2 = acc * t.inv_n;
   }
-  if (!(err <= 1.0)) {
+  if (!(err2 <= 1.0)) {
     s.c_rej_err++;
-    const double fac = isfinite(err) ? 0.9 * pow(err, -1.0 / (kk + 1)) : 0.2;
+    const double fac = finite_bits(err2) ? 0.9 * pow(err2, -0.5 / (kk + 1)) : 0.2;
     s.h = h * (fac > 0.2 ? fac : 0.2);
     return false;
   }
@@ -705,7 +712,7 @@ NB_HD inline bool zone_attempt(const Net& t, Zone& s, const WS& w,
     int best_q = k;
     // E_k is the step's own error estimate: the same extrapolation through
     // the same points at the same time, so the same bits
-    double best = step_factor(err, k);
+    double best = step_factor(err2, k);
     if (k > 1) {
       const double fq = step_factor(order_estimate(t, s, w, k - 1, h), k - 1);
       if (fq > best) { best = fq; best_q = k - 1; }
@@ -717,13 +724,35 @@ NB_HD inline bool zone_attempt(const Net& t, Zone& s, const WS& w,
     if (best_q != k) { s.k = best_q; s.nconsec = 0; }
     factor = best;
   } else {
-    factor = step_factor(err, kk);
+    factor = step_factor(err2, kk);
   }
   if (factor < 0.2) factor = 0.2;
   if (factor > 5.0) factor = 5.0;
   if (factor >= 1.0 && factor < 1.2) factor = 1.0;
   s.h = h * factor;
   return false;
+}
+
+// GPU global timer (ns)
+NB_HD __forceinline__ unsigned long long gpu_ns() {
+#ifdef __CUDA_ARCH__
+  unsigned long long v;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(v));
+  return v;
+#else
+  return 0ull;
+#endif
+}
+
+// A zone claimed after the watchdog budget ran out: outputs are its inputs.
+NB_HD inline void zone_timeout_unstarted(const Net& t, long long z, const BurnParams& P) {
+  for (int i = 0; i < t.N; ++i) P.Y[(size_t)z * t.N + i] = P.Y0[(size_t)z * t.N + i];
+  P.T9[z] = P.T9_0[z];
+  if (P.E) P.E[z] = 0.0;
+  P.status[z] = NB_Z_TIMEOUT;
+  if (P.use_tape) { P.tape.zstat[z] = NB_Z_TIMEOUT; P.tape.steps[z] = 0; }
+  if (P.counters)
+    for (int c = 0; c < NCOUNT; ++c) P.counters[(size_t)z * NCOUNT + c] = 0;
 }
 
 // write a finished zone

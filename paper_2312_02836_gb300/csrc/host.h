@@ -24,6 +24,8 @@ struct nb_net_s {
   size_t stage_bytes = 0;
   double* ws_adj = nullptr;   // adjoint per-lane workspace
   size_t ws_adj_bytes = 0;
+  unsigned char* sched = nullptr;   // claim-order keys, indices, sort scratch
+  size_t sched_bytes = 0;
   std::mutex mu;
 };
 

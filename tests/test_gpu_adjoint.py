@@ -83,15 +83,57 @@ def test_adjoint_matches_forward_sensitivity(name, Z):
         for q in range(K):
             w = gY[q, i]
             mag = np.abs(w) @ np.abs(Yf[i]) + abs(gE[q, i]) * abs(o["E"][i])
+            # Newton leaves every state entry within 1e-3 of its weight
+            # atol + rtol|Y| (C6), so the linearisation point of the frozen
+            # map - and the sensitivity of an output Y - is known to about
+            # 1e-3 w / |Y| relative; negligible unless Y is near atol
+            rt = 1e-7
+            if q > 0:
+                y = abs(Yf[i][top[i, q - 1]])
+                rt += 1e-3 * (s["atol"] + s["rtol"] * y) / max(y, 1e-300)
             exp_l = w @ dx[:net.N, :net.R] + gE[q, i] * dE[:net.R]
-            _check(exp_l, dl[q, i], 1e-7, out_mag=mag)
+            _check(exp_l, dl[q, i], rt, out_mag=mag)
             exp_y0 = w @ dx[:net.N, net.R:net.R + net.N] + gE[q, i] * dE[net.R:net.R + net.N]
-            _check(exp_y0, dY0[q, i], 1e-7, out_mag=mag)
+            _check(exp_y0, dY0[q, i], rt, out_mag=mag)
             col = net.R + net.N   # T9: initial state entry or parameter
             exp_t = w @ dx[:net.N, col] + gE[q, i] * dE[col]
-            _check(np.array([exp_t]), np.array([dT0[q, i]]), 1e-7,
+            _check(np.array([exp_t]), np.array([dT0[q, i]]), rt,
                    scale=np.abs(exp_y0).max() * max(1.0, abs(z["T9"][i])))
     assert same >= 0.9 * Z
+
+
+@pytest.mark.parametrize("name,zone", [("net48_adjoint", 2), ("chain13_heat", 0)])
+def test_adjoint_against_frozen_schedule_central_differences(name, zone):
+    # central differences of the exactly converged (full-Newton) frozen map,
+    # on the oracle's schedule; checked where the GPU took as many steps
+    nb, torch = nb_mod()
+    net, z, s = gen.problem(name, zone + 1)
+    zz = {k: v[zone:zone + 1] for k, v in z.items()}
+    tp = oracle.burn_tape(net, zz["Y"][0], zz["T9"][0], zz["rho"][0], s["t_end"],
+                          s["rtol"], s["atol"])
+    top = gen.largest_species(tp["x"][-1:, :net.N], 2)[0]
+    gY = np.zeros((2, 1, net.N))
+    gY[0, 0, top[0]] = 1.0
+    gY[1, 0, top[1]] = 1.0
+    gE = np.zeros((2, 1)) if net.Q is not None else None
+    dl, dY0, dT0, cnt, Yf, st = _gpu_adjoint(nb, torch, net, zz, s, gY, gE,
+                                             np.zeros((2, 1)) if net.self_heating else None)
+    assert st[0] == 0 and cnt[0, 0] == tp["counters"][0]
+    rng = np.random.default_rng(4)
+    eps = 1e-4
+    for r in rng.choice(net.R, 3, replace=False):
+        def run(sign):
+            lm = np.zeros(net.R)
+            lm[r] = sign * eps
+            x, _ = oracle.replay(net, zz["Y"][0], zz["T9"][0], zz["rho"][0], tp["t"],
+                                 tp["k"], s["rtol"], s["atol"], ln_mult=lm)
+            return x
+        fd = (run(1) - run(-1)) / (2 * eps)
+        for q in range(2):
+            y = abs(tp["x"][-1][top[q]])
+            w = s["atol"] + s["rtol"] * y
+            tol = 1e-6 * abs(fd[top[q]]) + 1e-3 * w / y * abs(fd[top[q]]) + 1e-13 * y
+            assert abs(dl[q, 0, r] - fd[top[q]]) <= tol, (r, q, dl[q, 0, r], fd[top[q]])
 
 
 def test_adjoint_cotangent_sets_are_independent_and_linear():

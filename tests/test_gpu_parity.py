@@ -151,8 +151,12 @@ def test_deterministic_and_order_independent():
     d = gpu_run(nb, torch, net_c, z, s, threads_per_block=64, blocks_per_sm=1,
                 blob_in_shared=0)
     e = gpu_run(nb, torch, net_c, z, s, kernel="plain")
+    f = gpu_run(nb, torch, net_c, z, s, threads_per_block=224, ws_in_shared=3)
+    g = gpu_run(nb, torch, net_c, z, s, threads_per_block=96, ws_in_shared=3,
+                blocks_per_sm=2)
     for k in a:
-        assert np.array_equal(a[k], d[k]) and np.array_equal(a[k], e[k])
+        for other in (d, e, f, g):
+            assert np.array_equal(a[k], other[k])
 
 
 def test_rate_multipliers_shared_and_per_zone():
