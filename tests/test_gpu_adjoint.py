@@ -87,7 +87,11 @@ def test_adjoint_matches_forward_sensitivity(name, Z):
             # atol + rtol|Y| (C6), so the linearisation point of the frozen
             # map - and the sensitivity of an output Y - is known to about
             # 1e-3 w / |Y| relative; negligible unless Y is near atol
-            rt = 1e-7
+            # 1e-6: the GPU and the oracle linearise along trajectories that
+            # differ at the rounding level, and long stiff zones amplify that
+            # (one 868-step zone's energy gradient differs by 3e-7 between the
+            # oracle built on x86-64 and on aarch64, whose libm differ)
+            rt = 1e-6
             if q > 0:
                 y = abs(Yf[i][top[i, q - 1]])
                 rt += 1e-3 * (s["atol"] + s["rtol"] * y) / max(y, 1e-300)
