@@ -131,6 +131,13 @@ typedef struct {
                                step count, so the last zones claimed are
                                short and a warp's lanes get alike zones */
   int32_t reserved;
+  const double* t_end_zone; /* [Z] device array of per-zone end times, or NULL
+                               (every zone burns to t_end): operator-split use,
+                               each zone burning for its own hydro step.
+                               A negative or non-finite entry gives that zone
+                               NB_Z_NONFINITE.  nb_burn_batch and
+                               nb_burn_batch_host (a device pointer there too);
+                               ignored by nb_burn_batch_noalloc. */
   double time_budget_s;     /* > 0: device watchdog.  Every lane reads the GPU
                                timer between step attempts; once the budget,
                                counted from the start of its block, has run

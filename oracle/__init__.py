@@ -72,7 +72,7 @@ def _load():
             lib.ora_bdf_alpha.argtypes = [I32, D, P, D, P]
             lib.ora_extrapolate.argtypes = [I32, I32, P, P, D, P]
             lib.ora_burn_batch.argtypes = [P, P, I64, P, P, P, P, I32, P, P, P,
-                                           P, P, I32]
+                                           P, P, I32, P]
             lib.ora_burn_batch.restype = I32
             lib.ora_burn_tape.argtypes = [P, P, P, D, D, P, P, P, P, P, I32, P,
                                           P, P, P, P]
@@ -185,7 +185,8 @@ def extrapolate(t_pts, x_pts, t):
 
 
 def burn(net, Y0, T9, rho, t_end, rtol, atol, ln_mult=None, threads=0, **opts):
-    """Burn Z zones.  Returns dict(Y, T9, E, counters [Z, 8], status, threads)."""
+    """Burn Z zones.  t_end is a number or a per-zone array [Z].  Returns
+    dict(Y, T9, E, counters [Z, 8], status, threads)."""
     net = _net(net)
     lib = _load()
     Y0 = _f64(np.atleast_2d(Y0))
@@ -202,10 +203,14 @@ def burn(net, Y0, T9, rho, t_end, rtol, atol, ln_mult=None, threads=0, **opts):
     E = np.empty(Z)
     cnt = np.zeros((Z, N_COUNTERS), dtype=np.int32)
     st = np.zeros(Z, dtype=np.int32)
-    o = _opts(t_end, rtol, atol, **opts)
+    tz = None
+    if np.ndim(t_end) > 0:
+        tz = _f64(t_end)
+        t_end = 0.0
+    o = _opts(float(t_end), rtol, atol, **opts)
     used = lib.ora_burn_batch(net.ptr, C.addressof(o), Z, _p(Y0), _p(T9),
                               _p(rho), _p(lm), per_zone, _p(Y), _p(T9o), _p(E),
-                              _p(cnt), _p(st), int(threads))
+                              _p(cnt), _p(st), int(threads), _p(tz))
     return dict(Y=Y, T9=T9o, E=E, counters=cnt, status=st, threads=used)
 
 

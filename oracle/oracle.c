@@ -697,6 +697,7 @@ typedef struct {
     const ora_network* net;
     const ora_options* opt;
     int64_t Z;
+    const double* t_end_z;      /* per-zone end times or NULL */
     const double *Y0, *T9, *rho, *ln_mult;
     int per_zone_mult;
     double *Y, *T9_out, *E;
@@ -713,7 +714,18 @@ static void* batch_worker(void* arg) {
         if (z >= B->Z) break;
         const double* lm = B->ln_mult
             ? (B->per_zone_mult ? B->ln_mult + (size_t)z * net->R : B->ln_mult) : NULL;
-        B->status[z] = burn_zone(net, B->opt, B->Y0 + (size_t)z * net->N, B->T9[z],
+        ora_options oz = *B->opt;
+        if (B->t_end_z) oz.t_end = B->t_end_z[z];
+        if (!(oz.t_end >= 0.0) || !isfinite(oz.t_end)) {
+            /* a zone without a valid end time keeps its inputs */
+            memcpy(B->Y + (size_t)z * net->N, B->Y0 + (size_t)z * net->N, sizeof(double) * net->N);
+            if (B->T9_out) B->T9_out[z] = B->T9[z];
+            if (B->E) B->E[z] = 0.0;
+            memset(B->cnt + (size_t)z * C_COUNT, 0, sizeof(int32_t) * C_COUNT);
+            B->status[z] = ST_NONFINITE;
+            continue;
+        }
+        B->status[z] = burn_zone(net, &oz, B->Y0 + (size_t)z * net->N, B->T9[z],
                                  B->rho[z], lm, B->Y + (size_t)z * net->N,
                                  B->T9_out ? B->T9_out + z : NULL,
                                  B->E ? B->E + z : NULL,
@@ -725,19 +737,21 @@ static void* batch_worker(void* arg) {
 
 /* Burn Z zones.  Y0 [Z*N], T9 [Z], rho [Z]; ln_mult [R] shared or [Z*R];
    outputs Y [Z*N], T9_out [Z], E [Z] (may be NULL), cnt [Z*8], status [Z].
-   nthreads <= 0 means one thread per online core.  Returns the threads used. */
+   nthreads <= 0 means one thread per online core.  t_end_z: per-zone end
+   times (each zone burns for its own step) or NULL for opt->t_end.
+   Returns the threads used. */
 int ora_burn_batch(const ora_network* net, const ora_options* opt, int64_t Z,
                    const double* Y0, const double* T9, const double* rho,
                    const double* ln_mult, int per_zone_mult, double* Y,
                    double* T9_out, double* E, int32_t* cnt, int32_t* status,
-                   int nthreads) {
+                   int nthreads, const double* t_end_z) {
     if (nthreads <= 0) {
         long c = sysconf(_SC_NPROCESSORS_ONLN);
         nthreads = c > 0 ? (int)c : 1;
     }
     if (nthreads > Z) nthreads = Z > 0 ? (int)Z : 1;
     batch_t B;
-    B.net = net; B.opt = opt; B.Z = Z; B.Y0 = Y0; B.T9 = T9; B.rho = rho;
+    B.net = net; B.opt = opt; B.Z = Z; B.t_end_z = t_end_z; B.Y0 = Y0; B.T9 = T9; B.rho = rho;
     B.ln_mult = ln_mult; B.per_zone_mult = per_zone_mult; B.Y = Y;
     B.T9_out = T9_out; B.E = E; B.cnt = cnt; B.status = status;
     atomic_init(&B.next, 0);

@@ -138,6 +138,7 @@ def burn(net: Network, Y0, T9, rho, t_end: float, rtol: float, atol: float,
          ws_in_shared=-1, max_attempts=500000, time_budget_s=0.0, schedule=None,
          stream=None, out: Optional[BurnResult] = None):
     """Burn Z zones on the GPU.  Y0 [Z,N], T9 [Z], rho [Z] CUDA float64;
+    t_end a number, or a CUDA float64 tensor [Z] of per-zone end times;
     ln_mult None, [R] or [Z,R].  Returns BurnResult of CUDA tensors."""
     torch = _torch()
     Z = int(Y0.shape[0]) if Y0.dim() == 2 else 0
@@ -162,6 +163,11 @@ def burn(net: Network, Y0, T9, rho, t_end: float, rtol: float, atol: float,
                          torch.empty((Z,), dtype=torch.int32, device=dev))
     o = _options(kernel, threads_per_block, blocks_per_sm, blob_in_shared,
                  max_attempts, ws_in_shared, time_budget_s, schedule)
+    if isinstance(t_end, torch.Tensor):
+        # operator split: every zone burns for its own step
+        _dev(t_end, torch, "t_end", (Z,))
+        o.t_end_zone = t_end.data_ptr()
+        t_end = 0.0
     st = stream if stream is not None else torch.cuda.current_stream(dev)
     lib = _abi.load()
     ptr = lambda t: None if t is None else t.data_ptr()

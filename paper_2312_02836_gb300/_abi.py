@@ -53,7 +53,7 @@ class Options(C.Structure):
                 ("threads_per_block", C.c_int32), ("blocks_per_sm", C.c_int32),
                 ("blob_in_shared", C.c_int32), ("ws_in_shared", C.c_int32),
                 ("schedule", C.c_int32), ("reserved", C.c_int32),
-                ("time_budget_s", C.c_double)]
+                ("t_end_zone", C.c_void_p), ("time_budget_s", C.c_double)]
 
 
 def load(build_if_needed: bool = True):

@@ -279,7 +279,9 @@ extern "C" int nb_burn_adjoint(nb_net net, void* tape, int32_t K, const double* 
   A.o_mu = (int)off; off += n;
   A.o_de = (int)off; off += n;
   A.lane_doubles = off;
-  const int tpb = 128;
+  // one zone per lane; smaller blocks when there are few zones per SM
+  const long long per_sm = (Z + net->sm_count - 1) / net->sm_count;
+  const int tpb = per_sm >= 128 ? 128 : (int)std::max(32LL, per_sm / 32 * 32);
   cudaStream_t st = (cudaStream_t)stream;
   std::lock_guard<std::mutex> lk(net->mu);
   const size_t smem = (size_t)h.bytes;
@@ -289,7 +291,7 @@ extern "C" int nb_burn_adjoint(nb_net net, void* tape, int32_t K, const double* 
     CK(cudaFuncSetAttribute(k_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
   int occ = 0;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_adjoint, tpb, dyn));
-  long long blocks = (long long)std::max(1, std::min(occ, 4)) * net->sm_count;
+  long long blocks = (long long)std::max(1, std::min(occ, 2)) * net->sm_count;
   const long long needed = (Z + tpb - 1) / tpb;
   if (blocks > needed) blocks = needed;
   const size_t need = (size_t)blocks * tpb * A.lane_doubles * sizeof(double);

@@ -301,7 +301,12 @@ static int schedule_longest_first(nb_net net, BurnParams& P, long long lanes,
 // Launch one burn (device pointers).  Caller holds net->mu.
 static int launch_burn(nb_net net, BurnParams& P, const nb_options& o,
                        cudaStream_t st) {
-  const int tpb = o.threads_per_block > 0 ? o.threads_per_block : 128;
+  int tpb = o.threads_per_block > 0 ? o.threads_per_block : 128;
+  if (o.threads_per_block <= 0 && o.kernel != NB_KERNEL_PLAIN) {
+    // few zones: smaller blocks, so that every SM gets some
+    const long long per_sm = (P.Z + net->sm_count - 1) / net->sm_count;
+    if (per_sm < 128) tpb = (int)std::max(32LL, per_sm / 32 * 32);
+  }
   if (tpb % 32 != 0 || tpb > 256 || (o.kernel == NB_KERNEL_PLAIN && tpb > 128)) return NB_E_ARG;
   const size_t lane_bytes = (size_t)net->h.lane_doubles * sizeof(double);
   P.blob = net->d_blob;
@@ -389,6 +394,7 @@ extern "C" int nb_burn_batch(nb_net net, int64_t Z, const double* Y0, const doub
   P.max_attempts = o.max_attempts;
   if (!(o.time_budget_s >= 0.0)) return NB_E_ARG;
   P.budget_ns = o.time_budget_s > 0.0 ? (unsigned long long)(o.time_budget_s * 1e9) + 1ull : 0ull;
+  P.t_end_zone = o.t_end_zone;
   cudaStream_t st = (cudaStream_t)stream;
   std::lock_guard<std::mutex> lk(net->mu);
   if (tape) {
@@ -458,6 +464,7 @@ extern "C" int nb_burn_batch_host(nb_net net, int64_t Z, const double* Y0,
   P.max_attempts = o.max_attempts;
   if (!(o.time_budget_s >= 0.0)) return NB_E_ARG;
   P.budget_ns = o.time_budget_s > 0.0 ? (unsigned long long)(o.time_budget_s * 1e9) + 1ull : 0ull;
+  P.t_end_zone = o.t_end_zone;
   rc = launch_burn(net, P, o, st);
   if (rc) return rc;
   CK(cudaMemcpyAsync(Y, b + off_Y, zN, cudaMemcpyDeviceToHost, st));

@@ -165,12 +165,13 @@ struct BurnParams {
   int smem_warps;             // warps per block with hot arrays in shared memory
   unsigned long long budget_ns;  // watchdog budget per block, 0 = none
   const int32_t* order;       // claim order (zone index per claim), or null
+  const double* t_end_zone;   // [Z] per-zone end time (operator split), or null
 };
 
 // Register state of the zone a lane is integrating.
 struct Zone {
   long long z;
-  double t, h, E, T9f, rho, rho2;
+  double t, h, E, T9f, rho, rho2, tend;
   const double* lnm;
   int k, nh, hh, nconsec, nfail, status;
   int c_acc, c_rej_err, c_rej_newton, c_newton, c_jac, c_rhs, c_teval, c_edot;
@@ -514,8 +515,10 @@ NB_HD inline bool zone_init(const Net& t, Zone& s, const WS& w, const BurnParams
   s.rho = P.rho[z];
   s.rho2 = s.rho * s.rho;
   s.lnm = P.lnm ? (P.lnm_per_zone ? P.lnm + (size_t)z * t.R : P.lnm) : nullptr;
+  s.tend = P.t_end_zone ? P.t_end_zone[z] : P.t_end;
   const LV x0{w.xh.p};  // history slot 0
-  bool fin = isfinite(s.T9f) && s.T9f > 0.0 && isfinite(s.rho);
+  bool fin = isfinite(s.T9f) && s.T9f > 0.0 && isfinite(s.rho) && finite_bits(s.tend) &&
+             s.tend >= 0.0;
   for (int i = 0; i < N; ++i) {
     const double y = P.Y0[(size_t)z * N + i];
     x0[i] = y;
@@ -538,7 +541,7 @@ NB_HD inline bool zone_init(const Net& t, Zone& s, const WS& w, const BurnParams
   for (int r = 0; r < t.R; ++r) fin = fin && finite_bits(w.k[r]);
   for (int i = 0; i < n; ++i) fin = fin && finite_bits(w.f0[i]);
   if (!fin) { s.status = NB_Z_NONFINITE; return true; }
-  if (!(P.t_end > 0.0)) return true;
+  if (!(s.tend > 0.0)) return true;
   // starting step: Hairer-Norsett-Wanner I, Sec. II.4, p = 1
   double s0 = 0.0, s1 = 0.0;
   for (int i = 0; i < n; ++i) {
@@ -550,7 +553,7 @@ NB_HD inline bool zone_init(const Net& t, Zone& s, const WS& w, const BurnParams
   }
   const double d0 = sqrt(s0 / n), d1 = sqrt(s1 / n);
   double hp = (d0 < 1e-5 || d1 < 1e-5) ? 1e-6 : 0.01 * d0 / d1;
-  if (hp > P.t_end) hp = P.t_end;
+  if (hp > s.tend) hp = s.tend;
   for (int i = 0; i < n; ++i) w.x[i] = fma(hp, w.f0[i], x0[i]);
   if (t.sh) { eval_rates(t, s, w, w.x[N], false); s.c_teval++; }
   eval_terms(t, w, w.x);
@@ -566,8 +569,8 @@ NB_HD inline bool zone_init(const Net& t, Zone& s, const WS& w, const BurnParams
   const double dm = fmax(d1, d2);
   const double h1 = dm <= 1e-15 ? fmax(1e-6, hp * 1e-3) : sqrt(0.01 / dm);
   double h = fmin(100.0 * hp, h1);
-  if (h > P.t_end) h = P.t_end;
-  if (!(h >= 1e-30 * P.t_end)) h = 1e-30 * P.t_end;
+  if (h > s.tend) h = s.tend;
+  if (!(h >= 1e-30 * s.tend)) h = 1e-30 * s.tend;
   s.h = h;
   return false;
 }
@@ -583,12 +586,12 @@ NB_HD inline bool zone_attempt(const Net& t, Zone& s, const WS& w,
     return true;
   }
   double h = s.h;
-  if (h < 1e-30 * P.t_end || h < 1e-14 * s.t) {
+  if (h < 1e-30 * s.tend || h < 1e-14 * s.t) {
     s.status = NB_Z_DT_UNDERFLOW;
     return true;
   }
   double t_new;
-  if (s.t + h >= P.t_end) { h = P.t_end - s.t; t_new = P.t_end; }
+  if (s.t + h >= s.tend) { h = s.tend - s.t; t_new = s.tend; }
   else t_new = s.t + h;
   const int kk = s.k < s.nh ? s.k : s.nh;
 
@@ -703,7 +706,7 @@ NB_HD inline bool zone_attempt(const Net& t, Zone& s, const WS& w,
   s.E = E_new;
   s.c_acc++;
   if (!tape_record(t, P, s, w.x, h, kk)) { s.status = NB_Z_TAPE_FULL; return true; }
-  if (s.t >= P.t_end) { s.h = h; return true; }
+  if (s.t >= s.tend) { s.h = h; return true; }
   // next step size and order
   s.nconsec++;
   double factor;

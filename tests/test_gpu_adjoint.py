@@ -47,13 +47,13 @@ def _gpu_adjoint(nb, torch, net, z, s, gY, gE, gT9, ln_mult=None, max_steps=2000
             fw.counters.cpu().numpy(), fw.Y.cpu().numpy(), fw.status.cpu().numpy())
 
 
-def _check(expect, got, rtol, scale=None, out_mag=0.0):
+def _check(expect, got, rtol, scale=None, out_mag=0.0, abs_floor=0.0):
     # Entries far below the gradient's scale come from cancelling sums that
     # the two methods accumulate in different orders; a gradient of an
     # output O is known to ~1e-13 |O| absolute (rounding over ~10^3 steps).
     scale = (np.abs(expect).max() if scale is None else scale) + 1e-300
     err = np.abs(got - expect)
-    bad = err > rtol * np.abs(expect) + 1e-8 * scale + 1e-13 * out_mag
+    bad = err > rtol * np.abs(expect) + 1e-8 * scale + 1e-13 * out_mag + abs_floor
     assert not bad.any(), (np.where(bad), got[bad][:4], expect[bad][:4])
 
 
@@ -92,17 +92,24 @@ def test_adjoint_matches_forward_sensitivity(name, Z):
             # (one 868-step zone's energy gradient differs by 3e-7 between the
             # oracle built on x86-64 and on aarch64, whose libm differ)
             rt = 1e-6
+            floor = 0.0
             if q > 0:
                 y = abs(Yf[i][top[i, q - 1]])
-                rt += 1e-3 * (s["atol"] + s["rtol"] * y) / max(y, 1e-300)
+                wy = s["atol"] + s["rtol"] * y
+                rt += 1e-3 * wy / max(y, 1e-300)
+                if y < 1e3 * s["atol"]:
+                    # an output below ~1e3 atol is resolved by the method only
+                    # to about its weight (error test: w; Newton: 1e-3 w per
+                    # step, accumulated): its gradient is held to 1e-2 w
+                    floor = 1e-2 * wy
             exp_l = w @ dx[:net.N, :net.R] + gE[q, i] * dE[:net.R]
-            _check(exp_l, dl[q, i], rt, out_mag=mag)
+            _check(exp_l, dl[q, i], rt, out_mag=mag, abs_floor=floor)
             exp_y0 = w @ dx[:net.N, net.R:net.R + net.N] + gE[q, i] * dE[net.R:net.R + net.N]
-            _check(exp_y0, dY0[q, i], rt, out_mag=mag)
+            _check(exp_y0, dY0[q, i], rt, out_mag=mag, abs_floor=floor)
             col = net.R + net.N   # T9: initial state entry or parameter
             exp_t = w @ dx[:net.N, col] + gE[q, i] * dE[col]
             _check(np.array([exp_t]), np.array([dT0[q, i]]), rt,
-                   scale=np.abs(exp_y0).max() * max(1.0, abs(z["T9"][i])))
+                   scale=np.abs(exp_y0).max() * max(1.0, abs(z["T9"][i])), abs_floor=floor)
     assert same >= 0.9 * Z
 
 

@@ -180,3 +180,21 @@ def test_host_entry_point_matches_device_entry_point():
     h = nb.burn_host(net_c, z["Y"], z["T9"], z["rho"], s["t_end"], s["rtol"], s["atol"])
     for k in a:
         assert np.array_equal(a[k], h[k])
+
+
+def test_operator_split_per_zone_end_times():
+    # every zone burns for its own hydro step (log-uniform 1e-6 .. 1e-3 s)
+    nb, torch = nb_mod()
+    net, z, s = gen.problem("chain13_heat", 1500)
+    tz = np.exp(np.random.default_rng(21).uniform(np.log(1e-6), np.log(1e-3), 1500))
+    tz[7] = np.nan
+    tz[8] = -1.0
+    dev = torch.device("cuda")
+    g = nb.burn(nb.Network(net), torch.from_numpy(z["Y"]).to(dev),
+                torch.from_numpy(z["T9"]).to(dev), torch.from_numpy(z["rho"]).to(dev),
+                torch.from_numpy(tz).to(dev), s["rtol"], s["atol"])
+    torch.cuda.synchronize()
+    g = to_numpy(g)
+    o = oracle.burn(net, z["Y"], z["T9"], z["rho"], tz, s["rtol"], s["atol"])
+    assert g["status"][7] == 5 and g["status"][8] == 5
+    print(compare(g, o, s["atol"]))

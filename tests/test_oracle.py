@@ -452,3 +452,21 @@ def test_sensitivity_against_frozen_schedule_fd(name, zone):
         assert np.all(np.abs(col - fd) <= 1e-6 * np.abs(col) + floor), (p, col, fd)
         if net.Q is not None:
             assert abs(colE - fdE) <= 1e-6 * abs(colE) + 1e-8 * abs(Ep), (p, colE, fdE)
+
+
+def test_per_zone_end_times_equal_separate_burns():
+    # the operator-split mode: each zone burns for its own step
+    net, z, s = gen.problem("chain13_heat", 6)
+    tz = np.array([1e-4, 3e-4, 1e-3, 0.0, 2e-5, 7e-4])
+    a = oracle.burn(net, z["Y"], z["T9"], z["rho"], tz, s["rtol"], s["atol"])
+    for i in range(6):
+        b = oracle.burn(net, z["Y"][i:i + 1], z["T9"][i], z["rho"][i], tz[i], s["rtol"],
+                        s["atol"])
+        for key in ("Y", "T9", "E", "counters", "status"):
+            assert np.array_equal(a[key][i], b[key][0])
+    bad = tz.copy()
+    bad[1] = np.nan
+    bad[2] = -1.0
+    c = oracle.burn(net, z["Y"], z["T9"], z["rho"], bad, s["rtol"], s["atol"])
+    assert list(c["status"][1:3]) == [5, 5]
+    assert np.array_equal(c["Y"][1:3], z["Y"][1:3])
