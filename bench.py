@@ -53,11 +53,18 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(Z, launch):
-    """DRAM bytes per launch from the committed ncu summary, or None when the
-    kernel sources, the zone count or the launch shape differ from the
-    profiled ones."""
-    path = os.path.join(ROOT, "profiles", "k_burn_persistent_chain13_heat.md")
+def launch_shape(launch, variant):
+    """tpb,bps,ws_in_shared,specialised variant of a persistent launch."""
+    return "%d,%d,%d,%d" % (launch.get("threads_per_block", 0) or 128,
+                            launch.get("blocks_per_sm", 0) or 1,
+                            max(launch.get("ws_in_shared", 0), 0), variant)
+
+
+def profiled_traffic(kernel, Z, shape):
+    """DRAM bytes per launch from the committed ncu summary of this kernel,
+    or None when the kernel sources, the zone count or the launch shape
+    differ from the profiled ones."""
+    path = os.path.join(ROOT, "profiles", kernel + "_chain13_heat.md")
     if not os.path.exists(path):
         return None
     kv = {}
@@ -65,9 +72,6 @@ def profiled_traffic(Z, launch):
         if ":" in line and not line.startswith(("|", "#", " ")):
             k, v = line.split(":", 1)
             kv[k.strip()] = v.strip()
-    shape = "%d,%d,%d" % (launch.get("threads_per_block", 0) or 128,
-                          launch.get("blocks_per_sm", 0) or 1,
-                          max(launch.get("ws_in_shared", 0), 0))
     if (kv.get("source_hash") == kernel_source_hash() and kv.get("zones") == str(Z)
             and kv.get("launch") == shape and "dram_bytes_per_launch" in kv):
         return int(kv["dram_bytes_per_launch"])
@@ -226,10 +230,12 @@ def run_native(args):
             dist.barrier()
             torch.cuda.synchronize()
 
-    if args.blocks_per_sm or args.threads_per_block or args.ws_in_shared >= 0 or args.no_autotune:
+    if (args.blocks_per_sm or args.threads_per_block or args.ws_in_shared >= 0 or args.no_autotune
+            or args.specialize is not None):
         launch = dict(blocks_per_sm=args.blocks_per_sm,
                       threads_per_block=args.threads_per_block,
-                      ws_in_shared=args.ws_in_shared)
+                      ws_in_shared=args.ws_in_shared,
+                      specialize=0 if args.specialize is None else args.specialize)
         tune_ms = None
     else:
         from paper_2312_02836_gb300.autotune import autotune
@@ -258,6 +264,8 @@ def run_native(args):
     clk = clocks.stop() if clocks else None
     ms = [a.elapsed_time(b) for a, b in ev]
     mean_ms = max_over_ranks(statistics.mean(ms), dev)
+    variant = netc.info()["last_specialized"]
+    kname = "nb_spec_burn" if variant else "k_burn_persistent"
     counters = out.counters.cpu().numpy()
     status = out.status.cpu().numpy()
     ops = metrics.burn_ops(info, counters, net_spec.self_heating)
@@ -305,10 +313,10 @@ def run_native(args):
     # ---- roofline of the burn kernel (one launch per step)
     achieved = ops["flops"] / (mean_ms * 1e-3) / 1e12
     peak = metrics.FP64_PEAK_TFLOPS
-    traffic = profiled_traffic(Z, launch)
+    traffic = profiled_traffic(kname, Z, launch_shape(launch, variant))
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "kernel": "k_burn_persistent",
+                "kernel": kname,
                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2070 MHz",
                 "flops_per_launch": ops["flops"],
                 "special_functions_per_launch": ops["special"],
@@ -333,7 +341,9 @@ def run_native(args):
             "config": {"workload": WORKLOAD_DESC if workload == WORKLOAD else
                        workload_desc(workload, Z), "zones_per_gpu": Z,
                        "l2": "256 MiB buffer written between timed steps (L2 flush)",
-                       "kernel": "persistent lane-per-zone, device work queue",
+                       "kernel": ("persistent lane-per-zone, device work queue, "
+                                  + ("code generated for the network (storage variant %d)" % variant
+                                     if variant else "generic network walk")),
                        "launch": launch,
                        "autotune_ms": None if tune_ms is None else
                        [[c, round(m, 2)] for c, m in tune_ms]},
@@ -421,6 +431,8 @@ def main():
     p.add_argument("--blocks-per-sm", type=int, default=0)
     p.add_argument("--threads-per-block", type=int, default=0)
     p.add_argument("--ws-in-shared", type=int, default=-1)
+    p.add_argument("--specialize", type=int, default=None,
+                   help="-1 generic kernel, 0 automatic, 1..3 specialised variant")
     p.add_argument("--cpu-zones", type=int, default=8192)
     p.add_argument("--ref-zones", type=int, default=4096)
     p.add_argument("--no-cpu-baseline", action="store_true")

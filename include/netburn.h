@@ -37,8 +37,10 @@
 #ifndef NETBURN_H
 #define NETBURN_H
 
+#ifndef __CUDACC_RTC__ /* also read by the library's run-time compiled kernels */
 #include <stddef.h>
 #include <stdint.h>
+#endif
 
 #ifdef __cplusplus
 extern "C" {
@@ -52,6 +54,8 @@ extern "C" {
 #define NB_E_CUDA -4         /* a CUDA runtime call failed */
 #define NB_E_NOMEM -5        /* host or device allocation failed */
 #define NB_E_TAPE -6         /* tape missing, too small or from another net */
+#define NB_E_COMPILE -7      /* the network-specialised kernel could not be
+                                generated, compiled or loaded */
 
 /* per-zone status */
 #define NB_Z_OK 0
@@ -74,6 +78,7 @@ extern "C" {
 #define NB_C_RATE_EVALS 6    /* evaluations of all lambda_r(T9) */
 #define NB_C_EDOT 7          /* energy-only evaluations for E */
 
+#ifndef __CUDACC_RTC__ /* the run-time compiled kernels need only the codes above */
 typedef struct nb_net_s* nb_net;
 
 /* Network topology (host pointers, copied by nb_net_load). */
@@ -108,6 +113,10 @@ typedef struct {
   int64_t flops_edot;       /* edot from R_r (NB_C_EDOT) */
   int64_t flops_tsolve;     /* transposed solves of the adjoint, per cotangent */
   int32_t exp_per_rate_eval;
+  int32_t specialize_auto;  /* 1: burns with options.specialize = 0 use the
+                               network-specialised kernel (when it builds) */
+  int32_t last_specialized; /* storage variant of the specialised kernel the
+                               last burn ran, 0 = a generic kernel */
   int32_t reserved;
 } nb_net_info;
 
@@ -130,7 +139,15 @@ typedef struct {
                                claimed in increasing h0, which tracks their
                                step count, so the last zones claimed are
                                short and a warp's lanes get alike zones */
-  int32_t reserved;
+  int32_t specialize;       /* persistent kernel, generic or specialised:
+                               0 (default) automatic: the kernel generated
+                               for this network (see nb_net_specialize) when
+                               the network is small enough for it and it
+                               builds, else the generic kernel; -1 always the
+                               generic kernel; 1..3 the specialised kernel
+                               with that storage variant (NB_E_COMPILE when it
+                               cannot be built).  Ignored with ws_in_shared
+                               > 0 and by nb_burn_batch_noalloc. */
   const double* t_end_zone; /* [Z] device array of per-zone end times, or NULL
                                (every zone burns to t_end): operator-split use,
                                each zone burning for its own hydro step.
@@ -236,6 +253,34 @@ int nb_burn_batch_noalloc(nb_net net, int64_t Z, const double* Y0,
                           double* E, int32_t* counters, int32_t* status,
                           const nb_options* opt, void* stream);
 
+/* Network-specialised kernel.  The paper's pynucastro writes each network
+ * as its own code, every rate, RHS term and Jacobian entry spelled out
+ * (Sec. 2).  The generic kernel instead walks the compiled network from
+ * memory.  nb_net_specialize prints the network as straight-line CUDA (every
+ * coefficient a literal, every index a constant), compiles it for sm_103a
+ * with the CUDA run-time compiler (libnvrtc, loaded on first use) and loads
+ * it; burns then use it as options.specialize says.  It performs the
+ * generic kernel's floating-point operations in the same order, so both give
+ * the same bits.
+ *  variant  0: chosen from the network's sizes; 1: all Newton-loop arrays of
+ *           a zone in registers; 2: as 1 with the LU in the workspace;
+ *           3: only x, d, f in registers.
+ *  log      NULL or a host buffer of log_bytes for the compiler's log
+ *           (NUL-terminated, truncated to fit).
+ * Synchronous; compiling takes seconds.  NB_E_COMPILE on failure.  A kernel
+ * built once is kept with the network. */
+int nb_net_specialize(nb_net net, int32_t variant, char* log, int64_t log_bytes);
+/* The specialised kernel's source for a topology, without any GPU: host
+ * buffer buf of cap bytes (NUL-terminated when it fits); *len = source
+ * length in bytes (without the NUL).  NB_E_ARG when cap is too small (buf
+ * untouched, *len set). */
+int nb_specialize_source(const nb_topology* topo, const double* coeffs,
+                         int32_t variant, char* buf, int64_t cap, int64_t* len);
+/* Generate and compile the specialised kernel for a topology without any GPU
+ * (a build check): NB_OK or NB_E_COMPILE; log as for nb_net_specialize,
+ * including the register and spill report of the sm_103a assembler. */
+int nb_specialize_compile(const nb_topology* topo, const double* coeffs,
+                          int32_t variant, char* log, int64_t log_bytes);
 /* The FP64 exp the rate evaluation uses (Tang's table-driven method, see
  * the kernels' expf64.cuh), and optionally the CUDA library exp, on a device
  * array x [n]: y_tang [n] (and y_lib [n] unless NULL).  A diagnostic for
@@ -253,6 +298,7 @@ int nb_probe_fp64(int32_t active_lanes, int32_t iters, int32_t blocks_per_sm,
 
 const char* nb_strerror(int code);
 
+#endif /* __CUDACC_RTC__ */
 #ifdef __cplusplus
 }
 #endif

@@ -20,7 +20,7 @@ from . import _abi
 from ._abi import (COUNTER_NAMES, KERNEL_PERSISTENT, KERNEL_PLAIN, NCOUNT,
                    ZONE_STATUS, NetburnError)
 
-__all__ = ["Network", "burn", "burn_host", "BurnGraph", "Tape", "adjoint", "Burn",
+__all__ = ["Network", "specialized_source", "specialize_compile", "burn", "burn_host", "BurnGraph", "Tape", "adjoint", "Burn",
            "BurnResult", "NetburnError", "COUNTER_NAMES", "ZONE_STATUS",
            "KERNEL_PERSISTENT", "KERNEL_PLAIN", "library_path", "probe_fp64"]
 
@@ -41,6 +41,42 @@ def _np(a, dtype):
     return None if a is None else np.ascontiguousarray(a, dtype=dtype)
 
 
+def _topology(spec):
+    """(kept-alive arrays, nb_topology, coeffs pointer) of a network spec."""
+    arrays = dict(reac=_np(spec.reactants, np.int16), prod=_np(spec.products, np.int16),
+                  coef=_np(spec.coeffs, np.float64),
+                  Q=_np(getattr(spec, "Q", None), np.float64),
+                  scale=_np(getattr(spec, "scale", None), np.float64))
+    p = lambda a: None if a is None else a.ctypes.data
+    topo = _abi.Topology(int(spec.N), int(spec.R), p(arrays["reac"]), p(arrays["prod"]),
+                         p(arrays["Q"]), p(arrays["scale"]), int(bool(spec.self_heating)))
+    return arrays, topo, p(arrays["coef"])
+
+
+def specialized_source(spec, variant: int = 0) -> str:
+    """CUDA source of the network-specialised burn kernel (host only)."""
+    lib = _abi.load()
+    arrays, topo, coef = _topology(spec)
+    n = C.c_int64()
+    lib.nb_specialize_source(C.byref(topo), coef, int(variant), None, 0, C.byref(n))
+    buf = C.create_string_buffer(n.value + 1)
+    _abi.check(lib.nb_specialize_source(C.byref(topo), coef, int(variant), buf,
+                                        n.value + 1, C.byref(n)), "nb_specialize_source")
+    return buf.value.decode()
+
+
+def specialize_compile(spec, variant: int = 0) -> str:
+    """Compile the specialised kernel for sm_103a without a GPU; returns the
+    compiler log (registers, spills).  Raises NetburnError on failure."""
+    lib = _abi.load()
+    arrays, topo, coef = _topology(spec)
+    log = C.create_string_buffer(1 << 16)
+    rc = lib.nb_specialize_compile(C.byref(topo), coef, int(variant), log, len(log))
+    if rc != _abi.NB_OK:
+        raise NetburnError("nb_specialize_compile: " + log.value.decode(errors="replace"))
+    return log.value.decode(errors="replace")
+
+
 class Network:
     """A compiled network on the current CUDA device.
 
@@ -54,18 +90,10 @@ class Network:
         self.N = int(spec.N)
         self.R = int(spec.R)
         self.self_heating = bool(spec.self_heating)
-        self._reac = _np(spec.reactants, np.int16)
-        self._prod = _np(spec.products, np.int16)
-        self._coef = _np(spec.coeffs, np.float64)
-        self._Q = _np(getattr(spec, "Q", None), np.float64)
-        self._scale = _np(getattr(spec, "scale", None), np.float64)
-        self.has_energy = self._Q is not None
-        p = lambda a: None if a is None else a.ctypes.data
-        topo = _abi.Topology(self.N, self.R, p(self._reac), p(self._prod),
-                             p(self._Q), p(self._scale), int(self.self_heating))
+        self._arrays, topo, coef = _topology(spec)
+        self.has_energy = getattr(spec, "Q", None) is not None
         h = C.c_void_p()
-        _abi.check(lib.nb_net_load(C.byref(topo), p(self._coef), C.byref(h)),
-                   "nb_net_load")
+        _abi.check(lib.nb_net_load(C.byref(topo), coef, C.byref(h)), "nb_net_load")
         self._h = h
         self.n = self.N + (1 if self.self_heating else 0)
 
@@ -81,6 +109,15 @@ class Network:
         _abi.check(lib.nb_net_get_info(self.handle, C.byref(out)), "nb_net_get_info")
         return {name: getattr(out, name) for name, _ in out._fields_
                 if name != "reserved"}
+
+    def specialize(self, variant: int = 0) -> str:
+        """Build the network-specialised kernel now (nb_net_specialize);
+        returns the compiler log."""
+        log = C.create_string_buffer(1 << 16)
+        rc = _abi.load().nb_net_specialize(self.handle, int(variant), log, len(log))
+        if rc != _abi.NB_OK:
+            raise NetburnError("nb_net_specialize: " + log.value.decode(errors="replace"))
+        return log.value.decode(errors="replace")
 
     def close(self):
         if getattr(self, "_h", None) is not None:
@@ -103,7 +140,8 @@ class BurnResult(NamedTuple):
 
 
 def _options(kernel, threads_per_block, blocks_per_sm, blob_in_shared,
-             max_attempts, ws_in_shared=-1, time_budget_s=0.0, schedule=None):
+             max_attempts, ws_in_shared=-1, time_budget_s=0.0, schedule=None,
+             specialize=0):
     o = _abi.Options()
     _abi.load().nb_default_options(C.byref(o))
     if isinstance(kernel, str):
@@ -117,6 +155,7 @@ def _options(kernel, threads_per_block, blocks_per_sm, blob_in_shared,
     o.time_budget_s = float(time_budget_s)
     if schedule is not None:
         o.schedule = {"fifo": 0, "longest_first": 1}.get(schedule, schedule)
+    o.specialize = {"auto": 0, "generic": -1, None: 0}.get(specialize, specialize)
     return o
 
 
@@ -136,10 +175,12 @@ def burn(net: Network, Y0, T9, rho, t_end: float, rtol: float, atol: float,
          ln_mult=None, *, kernel="persistent", tape: "Optional[Tape]" = None,
          threads_per_block=0, blocks_per_sm=0, blob_in_shared=-1,
          ws_in_shared=-1, max_attempts=500000, time_budget_s=0.0, schedule=None,
-         stream=None, out: Optional[BurnResult] = None):
+         specialize=0, stream=None, out: Optional[BurnResult] = None):
     """Burn Z zones on the GPU.  Y0 [Z,N], T9 [Z], rho [Z] CUDA float64;
     t_end a number, or a CUDA float64 tensor [Z] of per-zone end times;
-    ln_mult None, [R] or [Z,R].  Returns BurnResult of CUDA tensors."""
+    ln_mult None, [R] or [Z,R].  specialize: 0/"auto" the kernel generated
+    for the network when it qualifies, -1/"generic" the generic kernel, 1..3
+    a specialised storage variant.  Returns BurnResult of CUDA tensors."""
     torch = _torch()
     Z = int(Y0.shape[0]) if Y0.dim() == 2 else 0
     _dev(Y0, torch, "Y0", (Z, net.N))
@@ -162,7 +203,7 @@ def burn(net: Network, Y0, T9, rho, t_end: float, rtol: float, atol: float,
                          torch.empty((Z, NCOUNT), dtype=torch.int32, device=dev),
                          torch.empty((Z,), dtype=torch.int32, device=dev))
     o = _options(kernel, threads_per_block, blocks_per_sm, blob_in_shared,
-                 max_attempts, ws_in_shared, time_budget_s, schedule)
+                 max_attempts, ws_in_shared, time_budget_s, schedule, specialize)
     if isinstance(t_end, torch.Tensor):
         # operator split: every zone burns for its own step
         _dev(t_end, torch, "t_end", (Z,))
@@ -212,7 +253,7 @@ class BurnGraph:
 def burn_host(net: Network, Y0, T9, rho, t_end, rtol, atol, ln_mult=None, *,
               kernel="persistent", threads_per_block=0, blocks_per_sm=0,
               blob_in_shared=-1, ws_in_shared=-1, max_attempts=500000,
-              stream=None, out=None):
+              specialize=0, stream=None, out=None):
     """Burn from host (numpy) arrays through ``nb_burn_batch_host``: the
     library copies the inputs in, burns and copies the outputs back.
     Returns a dict of numpy arrays; ``out`` may supply preallocated (e.g.
@@ -229,7 +270,7 @@ def burn_host(net: Network, Y0, T9, rho, t_end, rtol, atol, ln_mult=None, *,
                    counters=np.empty((Z, NCOUNT), np.int32),
                    status=np.empty(Z, np.int32))
     o = _options(kernel, threads_per_block, blocks_per_sm, blob_in_shared,
-                 max_attempts, ws_in_shared)
+                 max_attempts, ws_in_shared, specialize=specialize)
     st = stream if stream is not None else torch.cuda.current_stream()
     p = lambda a: None if a is None else a.ctypes.data
     rc = _abi.load().nb_burn_batch_host(
@@ -264,6 +305,15 @@ class Tape:
     def _recorded(self, Z, ln_mult, t_end, rtol, atol):
         self.recorded = dict(Z=Z, per_zone=(ln_mult is not None and ln_mult.dim() == 2),
                              t_end=t_end, rtol=rtol, atol=atol)
+
+    def specialize(self, variant: int = 0) -> str:
+        """Build the network-specialised kernel now (nb_net_specialize);
+        returns the compiler log."""
+        log = C.create_string_buffer(1 << 16)
+        rc = _abi.load().nb_net_specialize(self.handle, int(variant), log, len(log))
+        if rc != _abi.NB_OK:
+            raise NetburnError("nb_net_specialize: " + log.value.decode(errors="replace"))
+        return log.value.decode(errors="replace")
 
     def close(self):
         if getattr(self, "_h", None) is not None:

@@ -12,7 +12,7 @@ _lib = None
 
 NB_OK = 0
 ERRORS = {-1: "NB_E_ARG", -2: "NB_E_TOPOLOGY", -3: "NB_E_TOO_LARGE",
-          -4: "NB_E_CUDA", -5: "NB_E_NOMEM", -6: "NB_E_TAPE"}
+          -4: "NB_E_CUDA", -5: "NB_E_NOMEM", -6: "NB_E_TAPE", -7: "NB_E_COMPILE"}
 ZONE_STATUS = {0: "OK", 1: "MAX_STEPS", 2: "DT_UNDERFLOW", 3: "NEWTON_FAIL",
                4: "TAPE_FULL", 5: "NONFINITE", 6: "TIMEOUT"}
 NCOUNT = 8
@@ -25,6 +25,7 @@ KERNEL_PLAIN = 1
 EXPORTS = ("nb_net_load", "nb_net_free", "nb_net_get_info", "nb_default_options",
            "nb_burn_batch", "nb_burn_batch_host", "nb_tape_alloc", "nb_tape_free",
            "nb_tape_steps", "nb_burn_adjoint", "nb_burn_batch_noalloc",
+           "nb_net_specialize", "nb_specialize_source", "nb_specialize_compile",
            "nb_exp_eval", "nb_probe_fp64", "nb_strerror")
 
 
@@ -45,14 +46,15 @@ class NetInfo(C.Structure):
                 ("flops_jacobian", C.c_int64), ("flops_lu", C.c_int64),
                 ("flops_solve", C.c_int64), ("flops_edot", C.c_int64),
                 ("flops_tsolve", C.c_int64),
-                ("exp_per_rate_eval", C.c_int32), ("reserved", C.c_int32)]
+                ("exp_per_rate_eval", C.c_int32), ("specialize_auto", C.c_int32),
+                ("last_specialized", C.c_int32), ("reserved", C.c_int32)]
 
 
 class Options(C.Structure):
     _fields_ = [("max_attempts", C.c_int32), ("kernel", C.c_int32),
                 ("threads_per_block", C.c_int32), ("blocks_per_sm", C.c_int32),
                 ("blob_in_shared", C.c_int32), ("ws_in_shared", C.c_int32),
-                ("schedule", C.c_int32), ("reserved", C.c_int32),
+                ("schedule", C.c_int32), ("specialize", C.c_int32),
                 ("t_end_zone", C.c_void_p), ("time_budget_s", C.c_double)]
 
 
@@ -81,6 +83,12 @@ def load(build_if_needed: bool = True):
         lib.nb_burn_batch_noalloc.argtypes = [P, I64, P, P, P, D, D, D, P, I32, P,
                                               P, P, P, P, P, P]
         lib.nb_burn_batch_noalloc.restype = C.c_int
+        lib.nb_net_specialize.argtypes = [P, I32, P, I64]
+        lib.nb_net_specialize.restype = C.c_int
+        lib.nb_specialize_source.argtypes = [P, P, I32, P, I64, P]
+        lib.nb_specialize_source.restype = C.c_int
+        lib.nb_specialize_compile.argtypes = [P, P, I32, P, I64]
+        lib.nb_specialize_compile.restype = C.c_int
         lib.nb_exp_eval.argtypes = [P, P, P, I64, P]
         lib.nb_exp_eval.restype = C.c_int
         lib.nb_probe_fp64.argtypes = [I32, I32, I32, P, P]

@@ -1,12 +1,18 @@
 """Launch-shape autotuner for the persistent burn kernel.
 
-The kernel maps one zone to one lane, so the tunables are how many zones are
-in flight per SM and where their work arrays live:
+The kernel maps one zone to one lane, so the tunables are which kernel runs,
+how many zones are in flight per SM and where their work arrays live:
 
-* ``ws_in_shared`` w: the first w warps of each block keep their Newton-loop
-  arrays in shared memory (history in global memory), the others keep
-  everything in the global workspace, which stays L2-resident only while
-  few lanes are in flight;
+* ``specialize``: -1 the generic kernel, which walks the compiled network
+  from memory; 1..3 the kernel generated for this network, with its work
+  arrays in registers (1), the LU in the workspace (2) or only x, d, f in
+  registers (3).  Specialised candidates are tried only for networks the
+  library would specialise by itself (their straight-line code compiles in
+  seconds);
+* ``ws_in_shared`` w (generic kernel): the first w warps of each block keep
+  their Newton-loop arrays in shared memory (history in global memory), the
+  others keep everything in the global workspace, which stays L2-resident
+  only while few lanes are in flight;
 * ``threads_per_block`` and ``blocks_per_sm``: zones in flight.  Fewer lanes
   than zones let the device queue refill lanes whose zone finished; more
   lanes hide more latency but grow the workspace beyond L2.
@@ -21,16 +27,19 @@ from typing import Optional
 
 _CACHE: dict = {}
 
-DEFAULT_CANDIDATES = (
-    dict(ws_in_shared=0, threads_per_block=128, blocks_per_sm=1),
-    dict(ws_in_shared=1, threads_per_block=160, blocks_per_sm=1),
-    dict(ws_in_shared=2, threads_per_block=192, blocks_per_sm=1),
-    dict(ws_in_shared=3, threads_per_block=224, blocks_per_sm=1),
-    dict(ws_in_shared=3, threads_per_block=256, blocks_per_sm=1),
-    dict(ws_in_shared=3, threads_per_block=96, blocks_per_sm=1),
-    dict(ws_in_shared=0, threads_per_block=64, blocks_per_sm=2),
-    dict(ws_in_shared=0, threads_per_block=128, blocks_per_sm=2),
+GENERIC_CANDIDATES = (
+    dict(specialize=-1, ws_in_shared=0, threads_per_block=128, blocks_per_sm=1),
+    dict(specialize=-1, ws_in_shared=1, threads_per_block=160, blocks_per_sm=1),
+    dict(specialize=-1, ws_in_shared=3, threads_per_block=96, blocks_per_sm=1),
+    dict(specialize=-1, ws_in_shared=0, threads_per_block=64, blocks_per_sm=2),
+    dict(specialize=-1, ws_in_shared=0, threads_per_block=128, blocks_per_sm=2),
 )
+
+SPECIALIZED_CANDIDATES = tuple(
+    dict(specialize=v, threads_per_block=tpb, blocks_per_sm=bps)
+    for v in (1, 2, 3) for tpb, bps in ((64, 1), (128, 1), (128, 2), (256, 1)))
+
+DEFAULT_CANDIDATES = GENERIC_CANDIDATES + SPECIALIZED_CANDIDATES
 
 
 def autotune(net, Y0, T9, rho, t_end, rtol, atol, ln_mult=None, *,
@@ -48,6 +57,8 @@ def autotune(net, Y0, T9, rho, t_end, rtol, atol, ln_mult=None, *,
     stream = torch.cuda.current_stream(dev)
     best, best_ms, timings = None, float("inf"), []
     out = None
+    if not net.info()["specialize_auto"]:
+        candidates = [c for c in candidates if c.get("specialize", 0) < 0]
     for cand in candidates:
         try:
             out = burn(net, Y0, T9, rho, t_end, rtol, atol, ln_mult, out=out, **cand)

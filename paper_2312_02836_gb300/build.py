@@ -9,8 +9,12 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libnetburn.so")
-SOURCES = ["burn.cu", "adjoint.cu", "noalloc.cu", "probe.cu", "netload.cpp"]
-HEADERS = ["blob.h", "device.cuh", "host.h", "expf64.cuh"]
+SOURCES = ["burn.cu", "adjoint.cu", "noalloc.cu", "probe.cu", "netload.cpp", "codegen.cpp"]
+HEADERS = ["blob.h", "device.cuh", "integrator.cuh", "host.h", "expf64.cuh", "codegen.h"]
+# headers the run-time compiler needs, embedded as text into the library
+# (name as written in the #include directive, path)
+EMBED = [("expf64.cuh", "csrc/expf64.cuh"), ("integrator.cuh", "csrc/integrator.cuh"),
+         ("blob.h", "csrc/blob.h"), ("../../include/netburn.h", "../include/netburn.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -27,15 +31,40 @@ def stale() -> bool:
     return any(os.path.getmtime(f) > t for f in _inputs())
 
 
+def _write_embedded() -> str:
+    """Write _build/nb_embedded.h: the run-time compiler's headers as raw
+    string literals."""
+    path = os.path.join(BUILD, "nb_embedded.h")
+    lines = ["// written by build.py: headers of the run-time compiled kernel", "#pragma once"]
+    names, srcs = [], []
+    for name, rel in EMBED:
+        with open(os.path.join(HERE, rel)) as f:
+            text = f.read()
+        if ")NBSRC" in text:
+            raise RuntimeError(rel + " contains the raw-string delimiter")
+        names.append('"%s"' % name)
+        srcs.append('R"NBSRC(' + text + ')NBSRC"')
+    lines.append("static const int kEmbedCount = %d;" % len(EMBED))
+    lines.append("static const char* const kEmbedNames[] = {%s};" % ", ".join(names))
+    lines.append("static const char* const kEmbedSources[] = {\n" + ",\n".join(srcs) + "};")
+    text = "\n".join(lines) + "\n"
+    old = open(path).read() if os.path.exists(path) else None
+    if old != text:
+        with open(path, "w") as f:
+            f.write(text)
+    return path
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     """Compile every translation unit in parallel, then link the shared
     library.  Returns the library path."""
     if not force and not stale():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
+    _write_embedded()
     nvcc = os.environ.get("NVCC", "nvcc")
-    common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-                     "-I", os.path.join(HERE, "..", "include")]
+    common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC",
+                     "-I", os.path.join(HERE, "..", "include"), "-I", BUILD]
     procs, objs = [], []
     for src in SOURCES:
         path = os.path.join(CSRC, src)
@@ -56,7 +85,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             raise RuntimeError("nvcc failed: " + " ".join(cmd))
     tmp = LIB + f".{os.getpid()}.tmp"
     subprocess.check_call([nvcc] + ARCH + ["-shared", "-o", tmp] + objs +
-                          ["-lcudart"])
+                          ["-lcudart", "-ldl"])
     os.replace(tmp, LIB)
     return LIB
 

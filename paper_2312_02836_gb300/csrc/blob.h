@@ -6,7 +6,9 @@
 // into shared memory (or read it through L1) and walk its gather programs;
 // nothing in it depends on the zone.
 #pragma once
+#ifndef __CUDACC_RTC__  // the run-time compiler has no system headers
 #include <stdint.h>
+#endif
 
 namespace nb {
 

@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "blob.h"
+#include "codegen.h"
 #include "device.cuh"
 #include "../../include/netburn.h"
 
@@ -63,53 +64,7 @@ __global__ void __launch_bounds__(256, 1) k_burn_persistent(BurnParams P) {
     w = make_ws(t, gbase + (long long)P.smem_warps * cold * WS_LANES +
                        (long long)(wib - P.smem_warps) * t.lane_doubles * WS_LANES + lane);
   }
-  Zone s;
-  s.z = -1;
-  bool active = false, retired = false, fresh = false;
-  const unsigned long long t_start = P.budget_ns ? gpu_ns() : 0ull;
-  for (;;) {
-    const unsigned need = __ballot_sync(0xffffffffu, !active && !retired);
-    if (need) {
-      const int leader = __ffs(need) - 1;
-      unsigned long long base = 0;
-      if (lane == leader) base = atomicAdd(P.queue, (unsigned long long)__popc(need));
-      base = __shfl_sync(0xffffffffu, base, leader);
-      if (!active && !retired) {
-        const unsigned long long z = base + __popc(need & ((1u << lane) - 1u));
-        if (z < (unsigned long long)P.Z) {
-          s.z = P.order ? (long long)P.order[z] : (long long)z;
-          active = true;
-          fresh = true;
-        } else {
-          retired = true;
-        }
-      }
-    }
-    if (__all_sync(0xffffffffu, retired)) break;
-    if (active) {
-      const bool expired = P.budget_ns && gpu_ns() - t_start > P.budget_ns;
-      bool done;
-      if (expired && fresh) {
-        zone_timeout_unstarted(t, s.z, P);
-        fresh = false;
-        active = false;
-        continue;
-      }
-      if (expired) {
-        s.status = NB_Z_TIMEOUT;
-        done = true;
-      } else if (fresh) {
-        done = zone_init(t, s, w, P);
-        fresh = false;
-      } else {
-        done = zone_attempt(t, s, w, P);
-      }
-      if (done) {
-        zone_finish(t, s, w, P);
-        active = false;
-      }
-    }
-  }
+  burn_claim_loop(t, w, P);
 }
 
 // Scheduling pre-pass: each zone's starting step h0 (the integrator's own
@@ -182,6 +137,7 @@ const char* nb_strerror(int code) {
     case NB_E_CUDA: return "CUDA runtime error";
     case NB_E_NOMEM: return "allocation failed";
     case NB_E_TAPE: return "tape missing, too small or from another network";
+    case NB_E_COMPILE: return "network-specialised kernel could not be generated, compiled or loaded";
     default: return "unknown error";
   }
 }
@@ -235,6 +191,8 @@ int nb_net_free(nb_net net) {
   if (net->stage) cudaFree(net->stage);
   if (net->ws_adj) cudaFree(net->ws_adj);
   if (net->sched) cudaFree(net->sched);
+  for (auto& sp : net->spec)
+    if (sp.lib) cudaLibraryUnload(sp.lib);
   delete net;
   return NB_OK;
 }
@@ -261,10 +219,91 @@ int nb_net_get_info(nb_net net, nb_net_info* o) {
   o->flops_solve = h.fl_solve;
   o->flops_edot = h.fl_edot;
   o->exp_per_rate_eval = h.n_exp_per_teval;
+  o->specialize_auto = specialize_auto_ok(h) ? 1 : 0;
+  o->last_specialized = net->last_spec;
   return NB_OK;
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ specialised kernel
+
+// The specialised kernel of `variant` (1..3) for this network, generated,
+// compiled and loaded on first use.  Caller holds net->mu.
+static int spec_get(nb_net net, int variant, const void** fn) {
+  nb_net_s::Spec& sp = net->spec[variant];
+  if (sp.state == 0) {
+    std::vector<char> cubin;
+    const std::string src = specialized_source(net->blob, variant);
+    int rc = compile_specialized(src, &cubin, &sp.log, false);
+    if (rc == NB_OK &&
+        (cudaLibraryLoadData(&sp.lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) !=
+             cudaSuccess ||
+         cudaLibraryGetKernel(&sp.kern, sp.lib, "nb_spec_burn") != cudaSuccess)) {
+      cudaGetLastError();
+      if (sp.lib) cudaLibraryUnload(sp.lib);
+      sp.lib = nullptr;
+      sp.kern = nullptr;
+      sp.log += "\nloading the compiled kernel failed";
+      rc = NB_E_COMPILE;
+    }
+    sp.state = rc == NB_OK ? 1 : -1;
+  }
+  if (sp.state != 1) return NB_E_COMPILE;
+  *fn = reinterpret_cast<const void*>(sp.kern);
+  return NB_OK;
+}
+
+static void copy_log(const std::string& s, char* log, int64_t cap) {
+  if (!log || cap <= 0) return;
+  const size_t n = std::min<size_t>(s.size(), (size_t)cap - 1);
+  std::memcpy(log, s.data(), n);
+  log[n] = '\0';
+}
+
+extern "C" int nb_net_specialize(nb_net net, int32_t variant, char* log, int64_t log_bytes) {
+  if (!net || variant < 0 || variant > 3) return NB_E_ARG;
+  std::lock_guard<std::mutex> lk(net->mu);
+  const int v = resolve_variant(net->h, variant);
+  const void* fn = nullptr;
+  const int rc = spec_get(net, v, &fn);
+  copy_log(net->spec[v].log, log, log_bytes);
+  return rc;
+}
+
+// build the blob of a topology on the host (the checks of nb_net_load)
+static int host_blob(const nb_topology* T, const double* coeffs, std::vector<uint8_t>* blob) {
+  if (!T || (T->n_reactions > 0 && (!coeffs || !T->reactants || !T->products))) return NB_E_ARG;
+  if (T->n_species < 1 || T->n_reactions < 0 || (T->self_heating && !T->Q)) return NB_E_ARG;
+  BlobHeader h;
+  return build_blob(T, coeffs, blob, &h);
+}
+
+extern "C" int nb_specialize_source(const nb_topology* T, const double* coeffs,
+                                    int32_t variant, char* buf, int64_t cap, int64_t* len) {
+  if (!len || variant < 0 || variant > 3) return NB_E_ARG;
+  std::vector<uint8_t> blob;
+  int rc = host_blob(T, coeffs, &blob);
+  if (rc) return rc;
+  const std::string src = specialized_source(blob, variant);
+  *len = (int64_t)src.size();
+  if (!buf || cap < (int64_t)src.size() + 1) return NB_E_ARG;
+  std::memcpy(buf, src.c_str(), src.size() + 1);
+  return NB_OK;
+}
+
+extern "C" int nb_specialize_compile(const nb_topology* T, const double* coeffs,
+                                     int32_t variant, char* log, int64_t log_bytes) {
+  if (variant < 0 || variant > 3) return NB_E_ARG;
+  std::vector<uint8_t> blob;
+  int rc = host_blob(T, coeffs, &blob);
+  if (rc) return rc;
+  std::string lg;
+  std::vector<char> cubin;
+  rc = compile_specialized(specialized_source(blob, variant), &cubin, &lg, true);
+  copy_log(lg, log, log_bytes);
+  return rc;
+}
 
 // Longest-first claim order: h0 of every zone (pre-pass over the workspace
 // lanes already allocated), then a radix sort of (h0, zone).  Sets P.order.
@@ -301,6 +340,7 @@ static int schedule_longest_first(nb_net net, BurnParams& P, long long lanes,
 // Launch one burn (device pointers).  Caller holds net->mu.
 static int launch_burn(nb_net net, BurnParams& P, const nb_options& o,
                        cudaStream_t st) {
+  net->last_spec = 0;
   int tpb = o.threads_per_block > 0 ? o.threads_per_block : 128;
   if (o.threads_per_block <= 0 && o.kernel != NB_KERNEL_PLAIN) {
     // few zones: smaller blocks, so that every SM gets some
@@ -320,6 +360,54 @@ static int launch_burn(nb_net net, BurnParams& P, const nb_options& o,
     P.blob_in_smem = 0;
     k_burn_plain<<<(unsigned)blocks, tpb, 0, st>>>(P);
     CK(cudaGetLastError());
+    return NB_OK;
+  }
+  // the specialised kernel: o.specialize > 0 asks for it, 0 takes it when
+  // the network qualifies and it builds
+  const void* spec_fn = nullptr;
+  int spec_variant = 0;
+  if (o.specialize > 3 || o.specialize < -1) return NB_E_ARG;
+  if (o.kernel == NB_KERNEL_PERSISTENT && o.ws_in_shared <= 0 && o.specialize >= 0) {
+    if (o.specialize > 0) {
+      int rc = spec_get(net, o.specialize, &spec_fn);
+      if (rc) return rc;
+      spec_variant = o.specialize;
+    } else if (specialize_auto_ok(net->h)) {
+      spec_variant = resolve_variant(net->h, 0);
+      if (spec_get(net, spec_variant, &spec_fn) != NB_OK) {
+        spec_fn = nullptr;
+        spec_variant = 0;
+      }
+    }
+  }
+  if (spec_fn) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, spec_fn, tpb, 0) != cudaSuccess) {
+      cudaGetLastError();
+      occ = 1;
+    }
+    if (occ < 1) return NB_E_TOO_LARGE;
+    int bps = o.blocks_per_sm > 0 ? std::min(o.blocks_per_sm, occ) : 1;
+    long long blocks = (long long)bps * net->sm_count;
+    const long long needed_blocks = (P.Z + tpb - 1) / tpb;
+    if (blocks > needed_blocks) blocks = needed_blocks;
+    size_t need = std::max<size_t>((size_t)blocks * tpb * lane_bytes, 256);
+    if (o.schedule == 1) need = std::max(need, (size_t)128 * lane_bytes);  // pre-pass lanes
+    int rc = nb::ensure((void**)&net->ws, &net->ws_bytes, need);
+    if (rc) return rc;
+    P.ws = net->ws;
+    P.queue = net->queue;
+    P.blob_in_smem = 0;
+    P.smem_warps = 0;
+    P.order = nullptr;
+    if (o.schedule == 1 && P.Z > 1) {
+      rc = schedule_longest_first(net, P, blocks * (long long)tpb, st);
+      if (rc) return rc;
+    }
+    CK(cudaMemsetAsync(net->queue, 0, sizeof(unsigned long long), st));
+    void* args[] = {&P};
+    CK(cudaLaunchKernel(spec_fn, dim3((unsigned)blocks), dim3(tpb), args, 0, st));
+    net->last_spec = spec_variant;
     return NB_OK;
   }
   const size_t blob_b = (size_t)net->h.bytes;

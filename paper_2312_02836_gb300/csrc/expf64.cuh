@@ -13,9 +13,11 @@
 // handed to the library exp.  Error bound: below 0.6 ulp (tested against
 // the CUDA exp on the GPU and against mpmath on the host).
 #pragma once
+#ifndef __CUDACC_RTC__  // the run-time compiler has no system headers
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
+#endif
 
 #ifndef NB_HD
 #define NB_HD __device__
@@ -45,7 +47,9 @@ namespace nb {
 #ifdef __CUDACC__
 __device__ const double g_exp2_table[64] = {NB_EXP2_TABLE};
 #endif
+#ifndef __CUDACC_RTC__
 static const double h_exp2_table[64] = {NB_EXP2_TABLE};
+#endif
 
 NB_HD __forceinline__ double exp_tang(double x) {
 #ifdef __CUDA_ARCH__

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "blob.h"
@@ -26,6 +27,15 @@ struct nb_net_s {
   size_t ws_adj_bytes = 0;
   unsigned char* sched = nullptr;   // claim-order keys, indices, sort scratch
   size_t sched_bytes = 0;
+  // network-specialised kernels by storage variant (1..3): 0 not built,
+  // 1 loaded, -1 failed (log kept)
+  struct Spec {
+    int state = 0;
+    cudaLibrary_t lib = nullptr;
+    cudaKernel_t kern = nullptr;
+    std::string log;
+  } spec[4];
+  int last_spec = 0;   // variant the last burn ran (0 generic)
   std::mutex mu;
 };
 

@@ -1,0 +1,677 @@
+// integrator.cuh -- the per-zone BDF/Newton integrator, independent of how
+// the network is evaluated.
+//
+// Every function here is a template over two types:
+//   NT  the network: sizes n (state), N (species), R (reactions), flags sh
+//       (self-heating), hasE (energy), inv_n = 1/n;
+//   WT  one lane's work arrays x, xp, psi, d, f, iw, tmp, f0 (length n),
+//       k, g, rr (length R), lu (LU slots) and the history xh [HMAX*n],
+//       eh [HMAX], th [HMAX]; each is indexable with operator[].
+// and calls the network-specific operations by unqualified name, so that the
+// overloads for NT are found at instantiation:
+//   eval_rates(t, s, w, T9, with_g)   k_r (and g_r = d ln lambda_r/dT9)
+//   eval_terms(t, w, v)               rr_r = k_r prod Y of the reactants
+//   eval_f(t, w, v, out)              out = f(v) from rr
+//   eval_edot(t, w)                   sum_r Q_r rr_r
+//   assemble_M(t, w, v, alpha0, h)    lu = alpha0 I - h J(v)
+//   factor_M(t, w)                    static-pivot LU of lu in place
+//   solve_M(t, w, v)                  v <- M^-1 v with the factored lu
+// Two network types exist: the generic one (device.cuh) walks a compiled
+// network held in memory; the specialised one is generated per network as
+// straight-line code with every index a constant and compiled at run time.
+// Both perform the same floating-point operations in the same order, so they
+// give the same bits.
+//
+// This header is also compiled by the run-time compiler, so it includes no
+// system header.
+#pragma once
+#include "blob.h"
+#include "../../include/netburn.h"
+
+#ifndef NB_HD
+#define NB_HD __device__
+#endif
+
+// Loops over the state vector are unrolled in the specialised kernel (their
+// trip counts are constants there, and unrolling keeps the work arrays in
+// registers); the generic kernel leaves them as loops.
+#ifdef NB_SPECIALIZED
+#define NB_UNROLL _Pragma("unroll")
+#else
+#define NB_UNROLL
+#endif
+
+namespace nb {
+
+// lane-strided view of one per-lane array
+struct LV {
+  double* p;
+  NB_HD __forceinline__ double& operator[](int i) const {
+    return p[i * WS_LANES];
+  }
+};
+
+// Tape written by a burn that will be differentiated.
+struct TapeDev {
+  double* rec;       // [Z, cap, n + 3]: t, h, x[0..n), E
+  int8_t* ord;       // [Z, cap] BDF order of the step (0 for the start point)
+  int32_t* steps;    // [Z] records written
+  int32_t* zstat;    // [Z] status the zone finished with
+  double* rho;       // [Z]
+  double* T9f;       // [Z] fixed temperature (or initial T9)
+  int32_t cap;
+};
+
+struct BurnParams {
+  const unsigned char* blob;
+  int blob_bytes, blob_in_smem;
+  long long Z;
+  const double *Y0, *T9_0, *rho;
+  double t_end, rtol, atol;
+  const double* lnm;
+  int lnm_per_zone;
+  double *Y, *T9, *E;
+  int32_t *counters, *status;
+  int max_attempts;
+  double* ws;                 // per-lane workspace, lane_doubles * 32 per warp
+  unsigned long long* queue;  // zone counter of the persistent kernel
+  TapeDev tape;
+  int use_tape;
+  int smem_warps;             // warps per block with hot arrays in shared memory
+  unsigned long long budget_ns;  // watchdog budget per block, 0 = none
+  const int32_t* order;       // claim order (zone index per claim), or null
+  const double* t_end_zone;   // [Z] per-zone end time (operator split), or null
+};
+
+// Register state of the zone a lane is integrating.
+struct Zone {
+  long long z;
+  double t, h, E, T9f, rho, rho2, tend;
+  const double* lnm;
+  int k, nh, hh, nconsec, nfail, status;
+  int c_acc, c_rej_err, c_rej_newton, c_newton, c_jac, c_rhs, c_teval, c_edot;
+};
+
+NB_HD __forceinline__ int hslot(const Zone& s, int j) {
+  int v = s.hh + j;
+  return v >= HMAX ? v - HMAX : v;
+}
+
+// Finite and nonzero, decided on the exponent bits with integer ops (FP64
+// compares would occupy the FP64 pipe).
+NB_HD __forceinline__ long long dbits(double v) {
+#ifdef __CUDA_ARCH__
+  return __double_as_longlong(v);
+#else
+  long long b;
+  memcpy(&b, &v, sizeof(b));
+  return b;
+#endif
+}
+NB_HD __forceinline__ bool finite_nonzero(double v) {
+  const long long b = dbits(v) & 0x7fffffffffffffffLL;
+  return b != 0 && b < 0x7ff0000000000000LL;
+}
+NB_HD __forceinline__ bool finite_bits(double v) {
+  return (dbits(v) & 0x7fffffffffffffffLL) < 0x7ff0000000000000LL;
+}
+
+// ---------------------------------------------------------------- model
+// pieces both network types share, so that their arithmetic is one text
+
+// Powers of T9 in the rate fit (and their T9-derivative factors)
+struct TPow {
+  double t13, iT, t23, it13, T53, lnT, d1, d2, d3, d5;
+};
+
+NB_HD __forceinline__ TPow t_powers(double T9, bool with_g) {
+  TPow p;
+  p.t13 = cbrt(T9);
+  p.iT = 1.0 / T9;
+  p.t23 = p.t13 * p.t13;
+  p.it13 = p.t23 * p.iT;          // T9^(-1/3) without a second division
+  p.T53 = T9 * p.t23;
+  p.lnT = log(T9);
+  p.d1 = p.d2 = p.d3 = p.d5 = 0.0;
+  if (with_g) {
+    p.d1 = -p.iT * p.iT;
+    p.d2 = (-1.0 / 3.0) * p.iT * p.it13;
+    p.d3 = (1.0 / 3.0) * p.it13 * p.it13;
+    p.d5 = (5.0 / 3.0) * p.t23;
+  }
+  return p;
+}
+
+// exponent a0 + a1/T9 + a2 T9^-1/3 + a3 T9^1/3 + a4 T9 + a5 T9^5/3 + a6 ln T9
+// as two independent partial sums
+NB_HD __forceinline__ double rate_exponent(double a0, double a1, double a2, double a3,
+                                           double a4, double a5, double a6,
+                                           const TPow& p, double T9) {
+  double e1 = fma(a1, p.iT, a0);
+  double e2 = a4 * T9;
+  e1 = fma(a2, p.it13, e1);
+  e2 = fma(a5, p.T53, e2);
+  e1 = fma(a3, p.t13, e1);
+  e2 = fma(a6, p.lnT, e2);
+  return e1 + e2;
+}
+
+// d ln lambda / dT9 of the same fit
+NB_HD __forceinline__ double rate_dlog(double a1, double a2, double a3, double a4,
+                                       double a5, double a6, const TPow& p) {
+  double g1 = fma(a1, p.d1, a4);
+  double g2 = a5 * p.d5;
+  g1 = fma(a2, p.d2, g1);
+  g2 = fma(a6, p.iT, g2);
+  g1 = fma(a3, p.d3, g1);
+  return g1 + g2;
+}
+
+// c_v = 1.5 sum_i Y_i + 1e-3 T9^3 (two interleaved partial sums)
+template <class NT, class V>
+NB_HD __forceinline__ double heat_capacity(const NT& t, const V& v) {
+  double s0 = 0.0, s1 = 0.0;
+  int i = 0;
+  NB_UNROLL
+  for (; i + 1 < t.N; i += 2) {
+    s0 += v[i];
+    s1 += v[i + 1];
+  }
+  if (i < t.N) s0 += v[i];
+  const double T9 = v[t.N];
+  return 1.5 * (s0 + s1) + 1e-3 * T9 * T9 * T9;
+}
+
+// Rows of the T9 equation in M: with S_j = sum_r Q_r dR_r/dx_j,
+// dfT/dY_j = S_j a1 + b1, dfT/dT9 = S_T a1 + b2
+struct TRow {
+  double a1, b1, b2;
+};
+
+NB_HD __forceinline__ TRow t_row(double ed, double cv, double T9) {
+  TRow r;
+  const double icv = 1.0 / cv;
+  const double fT = ed / cv;
+  r.a1 = icv;
+  r.b1 = -fT * 1.5 * icv;
+  r.b2 = -fT * (3e-3 * T9 * T9) * icv;
+  return r;
+}
+
+// ---------------------------------------------------------------- integrator
+
+// ||v||^2 = mean (v_i * iw_i)^2, two interleaved partial sums (the tests
+// compare squares, which spares a square root per norm)
+template <class NT, class WT, class V>
+NB_HD __forceinline__ double wnorm2(const NT& t, const WT& w, const V& v) {
+  double s0 = 0.0, s1 = 0.0;
+  int i = 0;
+  NB_UNROLL
+  for (; i + 1 < t.n; i += 2) {
+    const double q0 = v[i] * w.iw[i], q1 = v[i + 1] * w.iw[i + 1];
+    s0 = fma(q0, q0, s0);
+    s1 = fma(q1, q1, s1);
+  }
+  if (i < t.n) {
+    const double q = v[i] * w.iw[i];
+    s0 = fma(q, q, s0);
+  }
+  return (s0 + s1) * t.inv_n;
+}
+
+// Lagrange weights at time tt of the q+1 newest history points starting at
+// history index j0 (0 = newest)
+template <class WT>
+NB_HD __forceinline__ void lagrange_weights(const Zone& s, const WT& w, int j0,
+                                            int q, double tt, double* lw) {
+  double tp[KMAX + 2];
+#pragma unroll
+  for (int j = 0; j < KMAX + 2; ++j) tp[j] = (j <= q) ? w.th[hslot(s, j0 + j)] : 0.0;
+#pragma unroll
+  for (int j = 0; j < KMAX + 2; ++j) {
+    double num = 1.0, den = 1.0;
+#pragma unroll
+    for (int m = 0; m < KMAX + 2; ++m) {
+      if (m != j && m <= q && j <= q) {
+        num *= tt - tp[m];
+        den *= tp[j] - tp[m];
+      }
+    }
+    lw[j] = (j <= q) ? num / den : 0.0;
+  }
+}
+
+// out = value at tt of the degree-q polynomial through history j0..j0+q
+template <class NT, class WT, class V>
+NB_HD __forceinline__ void extrapolate(const NT& t, const Zone& s, const WT& w, int j0,
+                                       int q, double tt, V&& out) {
+  double lw[KMAX + 2];
+  lagrange_weights(s, w, j0, q, tt, lw);
+  int base[KMAX + 2];
+#pragma unroll
+  for (int j = 0; j < KMAX + 2; ++j) base[j] = hslot(s, j0 + j) * t.n;
+  NB_UNROLL
+  for (int i = 0; i < t.n; ++i) {
+    double acc = 0.0;
+#pragma unroll
+    for (int j = 0; j < KMAX + 2; ++j)
+      if (j <= q) acc = fma(lw[j], w.xh[base[j] + i], acc);
+    out[i] = acc;
+  }
+}
+
+// 0.9 E^(-1/(q+1)) from E^2
+NB_HD __forceinline__ double step_factor(double E2, int q) {
+  if (!(E2 > 0.0)) return 5.0;
+  return 0.9 * pow(E2, -0.5 / (q + 1));
+}
+
+// E_q^2 after acceptance: newest point vs extrapolation through the q+1 older
+template <class NT, class WT>
+NB_HD __forceinline__ double order_estimate(const NT& t, const Zone& s, WT& w, int q,
+                                            double h) {
+  extrapolate(t, s, w, 1, q, w.th[hslot(s, 0)], w.tmp);
+  const double c = h / (w.th[hslot(s, 0)] - w.th[hslot(s, q + 1)]);
+  const int b0 = hslot(s, 0) * t.n;
+  double acc = 0.0;
+  NB_UNROLL
+  for (int i = 0; i < t.n; ++i) {
+    const double v = c * (w.xh[b0 + i] - w.tmp[i]) * w.iw[i];
+    acc = fma(v, v, acc);
+  }
+  return acc * t.inv_n;   // E_q^2
+}
+
+// Record an accepted point (time, step, state, energy, order); false when
+// the zone's tape is full.
+template <class NT, class V>
+NB_HD __forceinline__ bool tape_record(const NT& t, const BurnParams& P, const Zone& s,
+                                       const V& x, double h, int ord) {
+  if (!P.use_tape) return true;
+  int32_t* cnt = P.tape.steps + s.z;
+  const int idx = *cnt;
+  if (idx >= P.tape.cap) return false;
+  double* rec = P.tape.rec + ((unsigned long long)s.z * P.tape.cap + idx) * (t.n + 3);
+  rec[0] = s.t;
+  rec[1] = h;
+  NB_UNROLL
+  for (int i = 0; i < t.n; ++i) rec[2 + i] = x[i];
+  rec[2 + t.n] = s.E;
+  P.tape.ord[(unsigned long long)s.z * P.tape.cap + idx] = (int8_t)ord;
+  *cnt = idx + 1;
+  return true;
+}
+
+// alpha_j = h l_j'(tau_0), Lagrange basis on tau_0..tau_kk (unused j -> 0)
+NB_HD __forceinline__ void bdf_alpha(int kk, const double* tau, double h, double* alpha) {
+  double acc = 0.0;
+#pragma unroll
+  for (int m = 1; m <= KMAX; ++m)
+    if (m <= kk) acc += 1.0 / (tau[0] - tau[m]);
+  alpha[0] = h * acc;
+#pragma unroll
+  for (int j = 1; j <= KMAX; ++j) {
+    double num = 1.0, den = 1.0;
+#pragma unroll
+    for (int m = 0; m <= KMAX; ++m) {
+      if (m != j && m <= kk && j <= kk) {
+        if (m != 0) num *= tau[0] - tau[m];
+        den *= tau[j] - tau[m];
+      }
+    }
+    alpha[j] = (j <= kk) ? h * num / den : 0.0;
+  }
+}
+
+// ---------------------------------------------------------------- zone start
+
+// Load zone s.z, evaluate f(x0) and the starting step.  Returns true when the
+// zone is already finished (bad input or t_end == 0).
+template <class NT, class WT>
+NB_HD __forceinline__ bool zone_init(const NT& t, Zone& s, WT& w, const BurnParams& P) {
+  const long long z = s.z;
+  const int n = t.n, N = t.N;
+  s.t = 0.0; s.E = 0.0; s.k = 1; s.nh = 1; s.hh = 0; s.nconsec = 0; s.nfail = 0;
+  s.status = NB_Z_OK;
+  s.c_acc = s.c_rej_err = s.c_rej_newton = s.c_newton = 0;
+  s.c_jac = s.c_rhs = s.c_teval = s.c_edot = 0;
+  s.T9f = P.T9_0[z];
+  s.rho = P.rho[z];
+  s.rho2 = s.rho * s.rho;
+  s.lnm = P.lnm ? (P.lnm_per_zone ? P.lnm + (unsigned long long)z * t.R : P.lnm) : nullptr;
+  s.tend = P.t_end_zone ? P.t_end_zone[z] : P.t_end;
+  auto& x0 = w.xh;  // history slot 0
+  bool fin = finite_bits(s.T9f) && s.T9f > 0.0 && finite_bits(s.rho) &&
+             finite_bits(s.tend) && s.tend >= 0.0;
+  NB_UNROLL
+  for (int i = 0; i < N; ++i) {
+    const double y = P.Y0[(unsigned long long)z * N + i];
+    x0[i] = y;
+    fin = fin && finite_bits(y);
+  }
+  if (t.sh) x0[N] = s.T9f;
+  w.th[0] = 0.0;
+  w.eh[0] = 0.0;
+  if (P.use_tape) {
+    P.tape.steps[z] = 0;
+    P.tape.rho[z] = s.rho;
+    P.tape.T9f[z] = s.T9f;
+    tape_record(t, P, s, x0, 0.0, 0);
+  }
+  eval_rates(t, s, w, s.T9f, false);
+  s.c_teval++;
+  eval_terms(t, w, x0);
+  eval_f(t, w, x0, w.f0);
+  s.c_rhs++;
+  NB_UNROLL
+  for (int r = 0; r < t.R; ++r) fin = fin && finite_bits(w.k[r]);
+  NB_UNROLL
+  for (int i = 0; i < n; ++i) fin = fin && finite_bits(w.f0[i]);
+  if (!fin) { s.status = NB_Z_NONFINITE; return true; }
+  if (!(s.tend > 0.0)) return true;
+  // starting step: Hairer-Norsett-Wanner I, Sec. II.4, p = 1
+  double s0 = 0.0, s1 = 0.0;
+  NB_UNROLL
+  for (int i = 0; i < n; ++i) {
+    const double iw = 1.0 / (P.atol + P.rtol * fabs(x0[i]));
+    w.iw[i] = iw;
+    const double a = x0[i] * iw, b = w.f0[i] * iw;
+    s0 = fma(a, a, s0);
+    s1 = fma(b, b, s1);
+  }
+  const double d0 = sqrt(s0 / n), d1 = sqrt(s1 / n);
+  double hp = (d0 < 1e-5 || d1 < 1e-5) ? 1e-6 : 0.01 * d0 / d1;
+  if (hp > s.tend) hp = s.tend;
+  NB_UNROLL
+  for (int i = 0; i < n; ++i) w.x[i] = fma(hp, w.f0[i], x0[i]);
+  if (t.sh) { eval_rates(t, s, w, w.x[N], false); s.c_teval++; }
+  eval_terms(t, w, w.x);
+  eval_f(t, w, w.x, w.f);
+  s.c_rhs++;
+  double s2 = 0.0;
+  const double ihp = 1.0 / hp;
+  NB_UNROLL
+  for (int i = 0; i < n; ++i) {
+    const double q = (w.f[i] - w.f0[i]) * ihp * w.iw[i];
+    s2 = fma(q, q, s2);
+  }
+  const double d2 = sqrt(s2 / n);
+  const double dm = fmax(d1, d2);
+  const double h1 = dm <= 1e-15 ? fmax(1e-6, hp * 1e-3) : sqrt(0.01 / dm);
+  double h = fmin(100.0 * hp, h1);
+  if (h > s.tend) h = s.tend;
+  if (!(h >= 1e-30 * s.tend)) h = 1e-30 * s.tend;
+  s.h = h;
+  return false;
+}
+
+// ---------------------------------------------------------------- one attempt
+
+// One step attempt.  Returns true when the zone is finished.
+template <class NT, class WT>
+NB_HD __forceinline__ bool zone_attempt(const NT& t, Zone& s, WT& w, const BurnParams& P) {
+  const int n = t.n, N = t.N;
+  if (s.c_acc + s.c_rej_err + s.c_rej_newton >= P.max_attempts) {
+    s.status = NB_Z_MAX_STEPS;
+    return true;
+  }
+  double h = s.h;
+  if (h < 1e-30 * s.tend || h < 1e-14 * s.t) {
+    s.status = NB_Z_DT_UNDERFLOW;
+    return true;
+  }
+  double t_new;
+  if (s.t + h >= s.tend) { h = s.tend - s.t; t_new = s.tend; }
+  else t_new = s.t + h;
+  const int kk = s.k < s.nh ? s.k : s.nh;
+
+  // alpha_j = h l_j'(t_new) over t_new, t_n, .., t_{n+1-kk}
+  double tau[KMAX + 1];
+  tau[0] = t_new;
+#pragma unroll
+  for (int j = 1; j <= KMAX; ++j) tau[j] = (j <= kk) ? w.th[hslot(s, j - 1)] : 0.0;
+  double alpha[KMAX + 1];
+  bdf_alpha(kk, tau, h, alpha);
+  // psi = sum_{j>=1} alpha_j x_{n+1-j}; weights from x_n
+  {
+    int base[KMAX];
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j) base[j] = hslot(s, j) * n;
+    NB_UNROLL
+    for (int i = 0; i < n; ++i) {
+      double acc = 0.0;
+#pragma unroll
+      for (int j = 1; j <= KMAX; ++j)
+        if (j <= kk) acc = fma(alpha[j], w.xh[base[j - 1] + i], acc);
+      w.psi[i] = acc;
+      w.iw[i] = 1.0 / (P.atol + P.rtol * fabs(w.xh[base[0] + i]));
+    }
+  }
+  // predictor
+  if (s.nh >= kk + 1) extrapolate(t, s, w, 0, kk, t_new, w.xp);
+  else if (s.nh >= 2) extrapolate(t, s, w, 0, s.nh - 1, t_new, w.xp);
+  else {
+    const int b0 = hslot(s, 0) * n;
+    NB_UNROLL
+    for (int i = 0; i < n; ++i) w.xp[i] = fma(h, w.f0[i], w.xh[b0 + i]);
+  }
+  NB_UNROLL
+  for (int i = 0; i < n; ++i) w.x[i] = w.xp[i];
+  // Jacobian at the predictor, M, LU
+  if (t.sh) { eval_rates(t, s, w, w.x[N], true); s.c_teval++; }
+  eval_terms(t, w, w.x);
+  assemble_M(t, w, w.x, alpha[0], h);
+  s.c_jac++;
+  bool ok = factor_M(t, w);
+  // modified Newton
+  bool converged = false;
+  double nrm_prev = 0.0;
+  for (int m = 0; ok && m < 4; ++m) {
+    if (m > 0) {
+      if (t.sh) { eval_rates(t, s, w, w.x[N], false); s.c_teval++; }
+      eval_terms(t, w, w.x);
+    }
+    eval_f(t, w, w.x, w.f);
+    s.c_rhs++;
+    NB_UNROLL
+    for (int i = 0; i < n; ++i)
+      w.d[i] = -(fma(alpha[0], w.x[i], w.psi[i]) - h * w.f[i]);
+    solve_M(t, w, w.d);
+    NB_UNROLL
+    for (int i = 0; i < n; ++i) w.x[i] += w.d[i];
+    s.c_newton++;
+    const double nrm2 = wnorm2(t, w, w.d);
+    if (!finite_bits(nrm2)) { ok = false; break; }
+    if (nrm2 <= 1e-6) { converged = true; break; }          // ||d|| <= 1e-3
+    if (m > 0) {
+      if (nrm2 > 0.81 * nrm_prev) { ok = false; break; }     // theta > 0.9
+      const double theta = sqrt(nrm2 / nrm_prev);
+      if (theta / (1.0 - theta) * sqrt(nrm2) <= 1e-3) { converged = true; break; }
+    }
+    nrm_prev = nrm2;
+  }
+  if (!converged) {
+    s.c_rej_newton++;
+    if (++s.nfail >= 10) { s.status = NB_Z_NEWTON_FAIL; return true; }
+    s.h = h * 0.25;
+    return false;
+  }
+  s.nfail = 0;
+  // local error estimate
+  const double c = s.nh >= kk + 1 ? h / (t_new - w.th[hslot(s, kk)]) : 0.5;
+  double err2;   // err^2
+  {
+    double acc = 0.0;
+    NB_UNROLL
+    for (int i = 0; i < n; ++i) {
+      const double v = c * (w.x[i] - w.xp[i]) * w.iw[i];
+      acc = fma(v, v, acc);
+    }
+    err2 = acc * t.inv_n;
+  }
+  if (!(err2 <= 1.0)) {
+    s.c_rej_err++;
+    const double fac = finite_bits(err2) ? 0.9 * pow(err2, -0.5 / (kk + 1)) : 0.2;
+    s.h = h * (fac > 0.2 ? fac : 0.2);
+    return false;
+  }
+  // accept
+  double E_new = 0.0;
+  if (t.hasE) {
+    if (t.sh) { eval_rates(t, s, w, w.x[N], false); s.c_teval++; }
+    eval_terms(t, w, w.x);
+    const double ed = eval_edot(t, w);
+    s.c_edot++;
+    double acc = 0.0;
+#pragma unroll
+    for (int j = 1; j <= KMAX; ++j)
+      if (j <= kk) acc = fma(alpha[j], w.eh[hslot(s, j - 1)], acc);
+    E_new = (h * ed - acc) / alpha[0];
+  }
+  // push the new point into the history ring
+  s.hh = s.hh == 0 ? HMAX - 1 : s.hh - 1;
+  {
+    const int b0 = s.hh * n;
+    NB_UNROLL
+    for (int i = 0; i < n; ++i) w.xh[b0 + i] = w.x[i];
+    w.th[s.hh] = t_new;
+    w.eh[s.hh] = E_new;
+  }
+  if (s.nh < HMAX) s.nh++;
+  s.t = t_new;
+  s.E = E_new;
+  s.c_acc++;
+  if (!tape_record(t, P, s, w.x, h, kk)) { s.status = NB_Z_TAPE_FULL; return true; }
+  if (s.t >= s.tend) { s.h = h; return true; }
+  // next step size and order
+  s.nconsec++;
+  double factor;
+  if (s.nconsec >= s.k + 1) {
+    const int k = s.k;
+    int best_q = k;
+    // E_k is the step's own error estimate: the same extrapolation through
+    // the same points at the same time, so the same bits
+    double best = step_factor(err2, k);
+    if (k > 1) {
+      const double fq = step_factor(order_estimate(t, s, w, k - 1, h), k - 1);
+      if (fq > best) { best = fq; best_q = k - 1; }
+    }
+    if (k < KMAX && s.nh >= k + 3) {
+      const double fq = step_factor(order_estimate(t, s, w, k + 1, h), k + 1);
+      if (fq > best) { best = fq; best_q = k + 1; }
+    }
+    if (best_q != k) { s.k = best_q; s.nconsec = 0; }
+    factor = best;
+  } else {
+    factor = step_factor(err2, kk);
+  }
+  if (factor < 0.2) factor = 0.2;
+  if (factor > 5.0) factor = 5.0;
+  if (factor >= 1.0 && factor < 1.2) factor = 1.0;
+  s.h = h * factor;
+  return false;
+}
+
+// GPU global timer (ns)
+NB_HD __forceinline__ unsigned long long gpu_ns() {
+#ifdef __CUDA_ARCH__
+  unsigned long long v;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(v));
+  return v;
+#else
+  return 0ull;
+#endif
+}
+
+// A zone claimed after the watchdog budget ran out: outputs are its inputs.
+template <class NT>
+NB_HD __forceinline__ void zone_timeout_unstarted(const NT& t, long long z,
+                                                  const BurnParams& P) {
+  for (int i = 0; i < t.N; ++i)
+    P.Y[(unsigned long long)z * t.N + i] = P.Y0[(unsigned long long)z * t.N + i];
+  P.T9[z] = P.T9_0[z];
+  if (P.E) P.E[z] = 0.0;
+  P.status[z] = NB_Z_TIMEOUT;
+  if (P.use_tape) { P.tape.zstat[z] = NB_Z_TIMEOUT; P.tape.steps[z] = 0; }
+  if (P.counters)
+    for (int c = 0; c < NCOUNT; ++c) P.counters[(unsigned long long)z * NCOUNT + c] = 0;
+}
+
+// write a finished zone
+template <class NT, class WT>
+NB_HD __forceinline__ void zone_finish(const NT& t, const Zone& s, const WT& w,
+                                       const BurnParams& P) {
+  const long long z = s.z;
+  const int b0 = hslot(s, 0) * t.n;
+  NB_UNROLL
+  for (int i = 0; i < t.N; ++i) P.Y[(unsigned long long)z * t.N + i] = w.xh[b0 + i];
+  P.T9[z] = t.sh ? w.xh[b0 + t.N] : s.T9f;
+  if (P.E) P.E[z] = w.eh[s.hh];
+  P.status[z] = s.status;
+  if (P.use_tape) P.tape.zstat[z] = s.status;
+  if (P.counters) {
+    int32_t* c = P.counters + (unsigned long long)z * NCOUNT;
+    c[C_ACC] = s.c_acc; c[C_REJ_ERR] = s.c_rej_err; c[C_REJ_NEWTON] = s.c_rej_newton;
+    c[C_NEWTON_IT] = s.c_newton; c[C_JAC] = s.c_jac; c[C_RHS] = s.c_rhs;
+    c[C_TEVAL] = s.c_teval; c[C_EDOT] = s.c_edot;
+  }
+}
+
+// The persistent lane-per-zone loop: every lane claims zones from the device
+// queue (one atomic per warp for all lanes that need a zone), initialises,
+// attempts steps and writes each zone back, and claims the next one as soon
+// as its zone is done.  A lane whose block ran past the watchdog budget ends
+// its zone with NB_Z_TIMEOUT (and every zone it claims afterwards).
+template <class NT, class WT>
+__device__ __forceinline__ void burn_claim_loop(const NT& t, WT& w, const BurnParams& P) {
+  const int lane = threadIdx.x & 31;
+  Zone s;
+  s.z = -1;
+  bool active = false, retired = false, fresh = false;
+  const unsigned long long t_start = P.budget_ns ? gpu_ns() : 0ull;
+  for (;;) {
+    const unsigned need = __ballot_sync(0xffffffffu, !active && !retired);
+    if (need) {
+      const int leader = __ffs(need) - 1;
+      unsigned long long base = 0;
+      if (lane == leader) base = atomicAdd(P.queue, (unsigned long long)__popc(need));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (!active && !retired) {
+        const unsigned long long z = base + __popc(need & ((1u << lane) - 1u));
+        if (z < (unsigned long long)P.Z) {
+          s.z = P.order ? (long long)P.order[z] : (long long)z;
+          active = true;
+          fresh = true;
+        } else {
+          retired = true;
+        }
+      }
+    }
+    if (__all_sync(0xffffffffu, retired)) break;
+    if (active) {
+      const bool expired = P.budget_ns && gpu_ns() - t_start > P.budget_ns;
+      bool done;
+      if (expired && fresh) {
+        zone_timeout_unstarted(t, s.z, P);
+        fresh = false;
+        active = false;
+        continue;
+      }
+      if (expired) {
+        s.status = NB_Z_TIMEOUT;
+        done = true;
+      } else if (fresh) {
+        done = zone_init(t, s, w, P);
+        fresh = false;
+      } else {
+        done = zone_attempt(t, s, w, P);
+      }
+      if (done) {
+        zone_finish(t, s, w, P);
+        active = false;
+      }
+    }
+  }
+}
+
+}  // namespace nb

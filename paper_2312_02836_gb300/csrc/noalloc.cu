@@ -65,43 +65,8 @@ __global__ void __launch_bounds__(128, 2) k_burn_noalloc(BurnParams P) {
   const Net t = make_net(blob);
   const int lane = threadIdx.x & 31;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const WS w = make_ws(t, P.ws + warp * (long long)t.lane_doubles * WS_LANES + lane);
-  Zone s;
-  s.z = -1;
-  bool active = false, retired = false, fresh = false;
-  for (;;) {
-    const unsigned need = __ballot_sync(0xffffffffu, !active && !retired);
-    if (need) {
-      const int leader = __ffs(need) - 1;
-      unsigned long long base = 0;
-      if (lane == leader) base = atomicAdd(P.queue, (unsigned long long)__popc(need));
-      base = __shfl_sync(0xffffffffu, base, leader);
-      if (!active && !retired) {
-        const unsigned long long z = base + __popc(need & ((1u << lane) - 1u));
-        if (z < (unsigned long long)P.Z) {
-          s.z = (long long)z;
-          active = true;
-          fresh = true;
-        } else {
-          retired = true;
-        }
-      }
-    }
-    if (__all_sync(0xffffffffu, retired)) break;
-    if (active) {
-      bool done;
-      if (fresh) {
-        done = zone_init(t, s, w, P);
-        fresh = false;
-      } else {
-        done = zone_attempt(t, s, w, P);
-      }
-      if (done) {
-        zone_finish(t, s, w, P);
-        active = false;
-      }
-    }
-  }
+  WS w = make_ws(t, P.ws + warp * (long long)t.lane_doubles * WS_LANES + lane);
+  burn_claim_loop(t, w, P);
 }
 
 }  // namespace

@@ -1,0 +1,64 @@
+"""The network-specialised kernel's generator and its run-time compilation,
+on the CPU (the CUDA run-time compiler needs no GPU).  Its results are
+checked against the generic kernel, bit for bit, by the GPU tests."""
+import ctypes as C
+import re
+
+import pytest
+
+import gen
+import paper_2312_02836_gb300 as nb
+from paper_2312_02836_gb300 import _abi
+
+
+def test_source_spells_out_the_network():
+    net = gen.network("chain13_heat")
+    src = nb.specialized_source(net, 0)
+    head = src.splitlines()[0]
+    assert "N = 13 species, R = 12 reactions, n = 14" in head
+    assert "storage variant 2" in head        # 7n + LU slots > 160: LU in memory
+    # one exponent, one rate and one derivative factor per reaction, with the
+    # fit coefficients as exact hexadecimal literals
+    assert len(re.findall(r"e = rate_exponent\(", src)) == net.R
+    assert len(re.findall(r"w\.k\[\d+\] = exp_tang\(e\)", src)) == net.R
+    assert len(re.findall(r"w\.g\[\d+\] = rate_dlog\(", src)) == net.R
+    a = net.coeffs[5]
+    assert float.hex(float(a[0])).replace("0x", "") in src.replace("0x", "")
+    # every reaction's term multiplies its reactants: 3 Y0 for the 3-alpha
+    # reaction, Y_i Y0 for the captures
+    assert "w.rr[0] = w.k[0] * v[0] * v[0] * v[0];" in src
+    assert "w.rr[1] = w.k[1] * v[0] * v[1];" in src or "w.rr[1] = w.k[1] * v[1] * v[0];" in src
+    assert "extern \"C\" __global__" in src and "nb_spec_burn" in src
+    # variants differ only in where work arrays live
+    assert "double lu[" in nb.specialized_source(net, 1)
+    assert "LV lu;" in nb.specialized_source(net, 2)
+    assert "LV psi, iw, xp, tmp;" in nb.specialized_source(net, 3)
+    # fixed temperature: no derivative factors, rates kept for the whole zone
+    src0 = nb.specialized_source(gen.network("chain13"), 1)
+    assert "rate_dlog" not in src0 and "LV k;" in src0
+
+
+def test_source_arguments_checked():
+    lib = _abi.load()
+    net = gen.network("chain13")
+    arrays, topo, coef = nb._topology(net)
+    n = C.c_int64()
+    assert lib.nb_specialize_source(None, coef, 0, None, 0, None) == -1
+    assert lib.nb_specialize_source(C.byref(topo), coef, 4, None, 0,
+                                    C.byref(n)) == -1
+    # a too-small buffer reports the needed length and fails
+    rc = lib.nb_specialize_source(C.byref(topo), coef, 0, None, 0,
+                                  C.byref(n))
+    assert rc == -1 and n.value > 1000
+
+
+def test_specialized_kernel_compiles_for_sm103a():
+    try:
+        log = nb.specialize_compile(gen.network("chain13_heat"), 0)
+    except nb.NetburnError as e:
+        if "libnvrtc not found" in str(e):
+            pytest.skip("no run-time compiler in this image")
+        raise
+    assert "nb_spec_burn" in log and "sm_103a" in log
+    m = re.search(r"Used (\d+) registers", log)
+    assert m and int(m.group(1)) <= 255

@@ -51,13 +51,21 @@ CASES = [("chain13", 4096), ("chain13_literal", 1024), ("chain13_heat", 2048),
          ("net48", 256), ("net48_adjoint", 128), ("net128_heat", 16)]
 
 
-@pytest.mark.parametrize("kernel", ["persistent", "plain"])
+# "persistent": the default persistent launch (the network-specialised kernel
+# where the network qualifies); "generic": the persistent launch forced onto
+# the generic kernel; "plain": one thread per zone
+KERNELS = {"persistent": dict(kernel="persistent"),
+           "generic": dict(kernel="persistent", specialize="generic"),
+           "plain": dict(kernel="plain")}
+
+
+@pytest.mark.parametrize("kernel", list(KERNELS))
 @pytest.mark.parametrize("name,Z", CASES)
 def test_parity_with_oracle(name, Z, kernel):
     nb, torch = nb_mod()
     net, z, s = gen.problem(name, Z)
     net_c = nb.Network(net)
-    g = gpu_run(nb, torch, net_c, z, s, kernel=kernel)
+    g = gpu_run(nb, torch, net_c, z, s, **KERNELS[kernel])
     o = oracle_run(name, Z)
     if name == "net128_heat":
         # Zones whose oracle Newton iteration ever stalls sit at the FP64
