@@ -26,6 +26,7 @@
 // system header.
 #pragma once
 #include "blob.h"
+#include "expf64.cuh"
 #include "../../include/netburn.h"
 
 #ifndef NB_HD
@@ -219,25 +220,59 @@ NB_HD __forceinline__ double wnorm2(const NT& t, const WT& w, const V& v) {
   return (s0 + s1) * t.inv_n;
 }
 
+// out_i = sum_{j<cnt} c_j xh[base_j + i], summed in increasing j.  Loops over
+// the history points run to the lane's own count (a warp runs as many
+// iterations as its highest-order lane), not to the maximum order with the
+// extra terms predicated off.  The specialised build accumulates in registers
+// over that loop; the generic one loops over i outside.  Same operations in
+// the same order either way.
+template <class NT, class WT, class V>
+NB_HD __forceinline__ void hist_combine(const NT& t, const WT& w, int cnt, const double* c,
+                                        const int* base, V&& out) {
+#ifdef NB_SPECIALIZED
+  double acc[NT::n];
+  NB_UNROLL
+  for (int i = 0; i < NT::n; ++i) acc[i] = 0.0;
+#pragma unroll 1
+  for (int j = 0; j < cnt; ++j) {
+    const double cj = c[j];
+    const int b = base[j];
+    NB_UNROLL
+    for (int i = 0; i < NT::n; ++i) acc[i] = fma(cj, w.xh[b + i], acc[i]);
+  }
+  NB_UNROLL
+  for (int i = 0; i < NT::n; ++i) out[i] = acc[i];
+#else
+  for (int i = 0; i < t.n; ++i) {
+    double acc = 0.0;
+    for (int j = 0; j < cnt; ++j) acc = fma(c[j], w.xh[base[j] + i], acc);
+    out[i] = acc;
+  }
+#endif
+}
+
 // Lagrange weights at time tt of the q+1 newest history points starting at
-// history index j0 (0 = newest)
+// history index j0 (0 = newest): lw[j] = prod_{m!=j} (tt - t_m)/(t_j - t_m)
 template <class WT>
 NB_HD __forceinline__ void lagrange_weights(const Zone& s, const WT& w, int j0,
                                             int q, double tt, double* lw) {
-  double tp[KMAX + 2];
-#pragma unroll
-  for (int j = 0; j < KMAX + 2; ++j) tp[j] = (j <= q) ? w.th[hslot(s, j0 + j)] : 0.0;
-#pragma unroll
-  for (int j = 0; j < KMAX + 2; ++j) {
+  double tp[KMAX + 2], e[KMAX + 2];
+#pragma unroll 1
+  for (int j = 0; j <= q; ++j) {
+    tp[j] = w.th[hslot(s, j0 + j)];
+    e[j] = tt - tp[j];
+  }
+#pragma unroll 1
+  for (int j = 0; j <= q; ++j) {
     double num = 1.0, den = 1.0;
-#pragma unroll
-    for (int m = 0; m < KMAX + 2; ++m) {
-      if (m != j && m <= q && j <= q) {
-        num *= tt - tp[m];
+#pragma unroll 1
+    for (int m = 0; m <= q; ++m) {
+      if (m != j) {
+        num *= e[m];
         den *= tp[j] - tp[m];
       }
     }
-    lw[j] = (j <= q) ? num / den : 0.0;
+    lw[j] = num / den;
   }
 }
 
@@ -248,22 +283,21 @@ NB_HD __forceinline__ void extrapolate(const NT& t, const Zone& s, const WT& w, 
   double lw[KMAX + 2];
   lagrange_weights(s, w, j0, q, tt, lw);
   int base[KMAX + 2];
-#pragma unroll
-  for (int j = 0; j < KMAX + 2; ++j) base[j] = hslot(s, j0 + j) * t.n;
-  NB_UNROLL
-  for (int i = 0; i < t.n; ++i) {
-    double acc = 0.0;
-#pragma unroll
-    for (int j = 0; j < KMAX + 2; ++j)
-      if (j <= q) acc = fma(lw[j], w.xh[base[j] + i], acc);
-    out[i] = acc;
-  }
+#pragma unroll 1
+  for (int j = 0; j <= q; ++j) base[j] = hslot(s, j0 + j) * t.n;
+  hist_combine(t, w, q + 1, lw, base, out);
 }
 
-// 0.9 E^(-1/(q+1)) from E^2
+// 0.9 E^(-1/(q+1)) from E^2, as 0.9 exp(-ln(E^2) / (2(q+1))): the factor only
+// sets the next step size, so the few-ulp exp/log route replaces the library
+// pow (which computes in extended precision, several times the FP64 work)
+NB_HD __forceinline__ double err_factor(double E2, int q) {
+  return 0.9 * exp_tang(log(E2) * (-0.5 / (q + 1)));
+}
+
 NB_HD __forceinline__ double step_factor(double E2, int q) {
   if (!(E2 > 0.0)) return 5.0;
-  return 0.9 * pow(E2, -0.5 / (q + 1));
+  return err_factor(E2, q);
 }
 
 // E_q^2 after acceptance: newest point vs extrapolation through the q+1 older
@@ -305,22 +339,24 @@ NB_HD __forceinline__ bool tape_record(const NT& t, const BurnParams& P, const Z
 // alpha_j = h l_j'(tau_0), Lagrange basis on tau_0..tau_kk (unused j -> 0)
 NB_HD __forceinline__ void bdf_alpha(int kk, const double* tau, double h, double* alpha) {
   double acc = 0.0;
-#pragma unroll
-  for (int m = 1; m <= KMAX; ++m)
-    if (m <= kk) acc += 1.0 / (tau[0] - tau[m]);
+#pragma unroll 1
+  for (int m = 1; m <= kk; ++m) acc += 1.0 / (tau[0] - tau[m]);
   alpha[0] = h * acc;
-#pragma unroll
-  for (int j = 1; j <= KMAX; ++j) {
+#pragma unroll 1
+  for (int j = 1; j <= kk; ++j) {
     double num = 1.0, den = 1.0;
-#pragma unroll
-    for (int m = 0; m <= KMAX; ++m) {
-      if (m != j && m <= kk && j <= kk) {
+#pragma unroll 1
+    for (int m = 0; m <= kk; ++m) {
+      if (m != j) {
         if (m != 0) num *= tau[0] - tau[m];
         den *= tau[j] - tau[m];
       }
     }
-    alpha[j] = (j <= kk) ? h * num / den : 0.0;
+    alpha[j] = h * num / den;
   }
+#pragma unroll
+  for (int j = 1; j <= KMAX; ++j)
+    if (j > kk) alpha[j] = 0.0;
 }
 
 // ---------------------------------------------------------------- zone start
@@ -428,24 +464,19 @@ NB_HD __forceinline__ bool zone_attempt(const NT& t, Zone& s, WT& w, const BurnP
   // alpha_j = h l_j'(t_new) over t_new, t_n, .., t_{n+1-kk}
   double tau[KMAX + 1];
   tau[0] = t_new;
-#pragma unroll
-  for (int j = 1; j <= KMAX; ++j) tau[j] = (j <= kk) ? w.th[hslot(s, j - 1)] : 0.0;
+#pragma unroll 1
+  for (int j = 1; j <= kk; ++j) tau[j] = w.th[hslot(s, j - 1)];
   double alpha[KMAX + 1];
   bdf_alpha(kk, tau, h, alpha);
   // psi = sum_{j>=1} alpha_j x_{n+1-j}; weights from x_n
   {
     int base[KMAX];
-#pragma unroll
-    for (int j = 0; j < KMAX; ++j) base[j] = hslot(s, j) * n;
+#pragma unroll 1
+    for (int j = 0; j < kk; ++j) base[j] = hslot(s, j) * n;
+    hist_combine(t, w, kk, alpha + 1, base, w.psi);
+    const int b0 = hslot(s, 0) * n;
     NB_UNROLL
-    for (int i = 0; i < n; ++i) {
-      double acc = 0.0;
-#pragma unroll
-      for (int j = 1; j <= KMAX; ++j)
-        if (j <= kk) acc = fma(alpha[j], w.xh[base[j - 1] + i], acc);
-      w.psi[i] = acc;
-      w.iw[i] = 1.0 / (P.atol + P.rtol * fabs(w.xh[base[0] + i]));
-    }
+    for (int i = 0; i < n; ++i) w.iw[i] = 1.0 / (P.atol + P.rtol * fabs(w.xh[b0 + i]));
   }
   // predictor
   if (s.nh >= kk + 1) extrapolate(t, s, w, 0, kk, t_new, w.xp);
@@ -511,7 +542,7 @@ NB_HD __forceinline__ bool zone_attempt(const NT& t, Zone& s, WT& w, const BurnP
   }
   if (!(err2 <= 1.0)) {
     s.c_rej_err++;
-    const double fac = finite_bits(err2) ? 0.9 * pow(err2, -0.5 / (kk + 1)) : 0.2;
+    const double fac = finite_bits(err2) ? err_factor(err2, kk) : 0.2;
     s.h = h * (fac > 0.2 ? fac : 0.2);
     return false;
   }
@@ -523,9 +554,8 @@ NB_HD __forceinline__ bool zone_attempt(const NT& t, Zone& s, WT& w, const BurnP
     const double ed = eval_edot(t, w);
     s.c_edot++;
     double acc = 0.0;
-#pragma unroll
-    for (int j = 1; j <= KMAX; ++j)
-      if (j <= kk) acc = fma(alpha[j], w.eh[hslot(s, j - 1)], acc);
+#pragma unroll 1
+    for (int j = 1; j <= kk; ++j) acc = fma(alpha[j], w.eh[hslot(s, j - 1)], acc);
     E_new = (h * ed - acc) / alpha[0];
   }
   // push the new point into the history ring
