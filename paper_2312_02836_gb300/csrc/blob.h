@@ -81,6 +81,8 @@ struct BlobHeader {
       fl_edot, fl_tsolve;
   int32_t n_exp_per_teval;
   int32_t hot_doubles;  // leading part of the per-lane layout kept hot
+  int32_t w_kp;         // k_r at the step's reference temperature (self-heating)
+  int32_t pad_;
 };
 
 }  // namespace nb

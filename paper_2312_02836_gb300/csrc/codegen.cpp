@@ -149,14 +149,13 @@ std::string specialized_source(const std::vector<uint8_t>& blob, int variant) {
   else o("  LV psi, iw, xp, tmp;\n");
   if (lu_reg) o("  double lu[%d];\n", nnz);
   else o("  LV lu;\n");
-  if (k_reg) o("  double k[%d], g[%d];\n", Rd, Rd);
+  if (k_reg) o("  double k[%d], g[%d], kp[%d];\n", Rd, Rd, Rd);
   else o("  LV k;\n");
   o("  LV f0, xh, eh, th;\n};\n\n");
 
   // ---- rates
-  o("NB_HD __forceinline__ void eval_rates(const GNet&, const Zone& s, GWS& w, double T9,"
-    " bool with_g) {\n  const TPow p = t_powers(T9, with_g);\n  const double* lnm = s.lnm;\n"
-    "  double e;\n");
+  o("NB_HD __forceinline__ void eval_rates(const GNet&, const Zone& s, GWS& w, const TPow& p,"
+    " double T9, bool with_g) {\n  const double* lnm = s.lnm;\n  double e;\n");
   for (int r = 0; r < R; ++r) {
     const double* a = coef + 7 * r;
     o("  e = rate_exponent(%s, %s, %s, %s, %s, %s, %s, p, T9);\n", lit(a[0]).c_str(),
@@ -169,6 +168,31 @@ std::string specialized_source(const std::vector<uint8_t>& blob, int variant) {
       o("  if (with_g) w.g[%d] = rate_dlog(%s, %s, %s, %s, %s, %s, p);\n", r,
         lit(a[1]).c_str(), lit(a[2]).c_str(), lit(a[3]).c_str(), lit(a[4]).c_str(),
         lit(a[5]).c_str(), lit(a[6]).c_str());
+  }
+  o("}\n\n");
+
+  // ---- rates near the attempt's reference temperature (self-heating)
+  o("NB_HD __forceinline__ void save_ref_rates(const GNet&, GWS& w) {\n");
+  if (sh)
+    for (int r = 0; r < R; ++r) o("  w.kp[%d] = w.k[%d];\n", r, r);
+  o("}\n\n");
+  o("NB_HD __forceinline__ void eval_rates_near(const GNet&, const Zone& s, GWS& w, double T9,"
+    " const TPow& ref, double T9ref) {\n");
+  if (sh) {
+    o("  const TPow p = t_powers(T9, false);\n  const DPhi d = delta_phi(p, ref, T9, T9ref);\n"
+      "  const double* lnm = s.lnm;\n  double de, e;\n");
+    for (int r = 0; r < R; ++r) {
+      const double* a = coef + 7 * r;
+      o("  de = rate_delta(%s, %s, %s, %s, %s, %s, d);\n", lit(a[1]).c_str(), lit(a[2]).c_str(),
+        lit(a[3]).c_str(), lit(a[4]).c_str(), lit(a[5]).c_str(), lit(a[6]).c_str());
+      o("  if (small_delta(de)) {\n    w.k[%d] = rate_near(w.kp[%d], de);\n  } else {\n", r, r);
+      o("    e = rate_exponent(%s, %s, %s, %s, %s, %s, %s, p, T9);\n", lit(a[0]).c_str(),
+        lit(a[1]).c_str(), lit(a[2]).c_str(), lit(a[3]).c_str(), lit(a[4]).c_str(),
+        lit(a[5]).c_str(), lit(a[6]).c_str());
+      o("    if (lnm) e += lnm[%d];\n", r);
+      const char* rp = nrho[r] == 0 ? "1.0" : (nrho[r] == 1 ? "s.rho" : "s.rho2");
+      o("    w.k[%d] = exp_tang(e) * (%s * %s);\n  }\n", r, rp, lit(scale[r]).c_str());
+    }
   }
   o("}\n\n");
 

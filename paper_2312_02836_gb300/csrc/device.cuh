@@ -38,7 +38,7 @@ struct Net {
   const Pivot* piv;
   const TriRow *fw, *bw, *tfw, *tbw;
   int w_x, w_xp, w_psi, w_d, w_f, w_iw, w_tmp, w_f0, w_xh, w_eh, w_th, w_k,
-      w_g, w_rr, w_dt, w_lu, lane_doubles, hot_doubles;
+      w_g, w_rr, w_kp, w_dt, w_lu, lane_doubles, hot_doubles;
 };
 
 template <class T>
@@ -76,7 +76,7 @@ NB_HD inline Net make_net(const unsigned char* b) {
   t.w_x = h->w_x; t.w_xp = h->w_xp; t.w_psi = h->w_psi; t.w_d = h->w_d;
   t.w_f = h->w_f; t.w_iw = h->w_iw; t.w_tmp = h->w_tmp; t.w_f0 = h->w_f0;
   t.w_xh = h->w_xh; t.w_eh = h->w_eh; t.w_th = h->w_th; t.w_k = h->w_k;
-  t.w_g = h->w_g; t.w_rr = h->w_rr; t.w_dt = h->w_dt; t.w_lu = h->w_lu;
+  t.w_g = h->w_g; t.w_rr = h->w_rr; t.w_kp = h->w_kp; t.w_dt = h->w_dt; t.w_lu = h->w_lu;
   t.lane_doubles = h->lane_doubles;
   t.hot_doubles = h->hot_doubles;
   return t;
@@ -86,7 +86,7 @@ NB_HD inline Net make_net(const unsigned char* b) {
 // shared memory (hot_base) while the rest stay in global memory (cold_base,
 // offsets relative to hot_doubles).
 struct WS {
-  LV x, xp, psi, d, f, iw, tmp, f0, xh, eh, th, k, g, rr, dt, lu;
+  LV x, xp, psi, d, f, iw, tmp, f0, xh, eh, th, k, g, rr, kp, dt, lu;
 };
 
 NB_HD __forceinline__ WS make_ws_split(const Net& t, double* hot_base, double* cold_base) {
@@ -100,6 +100,7 @@ NB_HD __forceinline__ WS make_ws_split(const Net& t, double* hot_base, double* c
   w.k.p = hot_base + t.w_k * WS_LANES;
   w.g.p = hot_base + t.w_g * WS_LANES;
   w.rr.p = hot_base + t.w_rr * WS_LANES;
+  w.kp.p = hot_base + t.w_kp * WS_LANES;
   w.dt.p = hot_base + t.w_dt * WS_LANES;
   w.lu.p = hot_base + t.w_lu * WS_LANES;
   w.tmp.p = cold_base + (t.w_tmp - t.hot_doubles) * WS_LANES;
@@ -126,6 +127,7 @@ NB_HD __forceinline__ WS make_ws(const Net& t, double* lane_base) {
   w.k.p = lane_base + t.w_k * WS_LANES;
   w.g.p = lane_base + t.w_g * WS_LANES;
   w.rr.p = lane_base + t.w_rr * WS_LANES;
+  w.kp.p = lane_base + t.w_kp * WS_LANES;
   w.dt.p = lane_base + t.w_dt * WS_LANES;
   w.lu.p = lane_base + t.w_lu * WS_LANES;
   return w;
@@ -133,10 +135,10 @@ NB_HD __forceinline__ WS make_ws(const Net& t, double* lane_base) {
 
 // ---------------------------------------------------------------- model
 
-// k_r (and g_r = d ln lambda_r / dT9 when with_g) for temperature T9
-NB_HD inline void eval_rates(const Net& t, const Zone& s, const WS& w,
+// k_r (and g_r = d ln lambda_r / dT9 when with_g) for temperature T9, whose
+// powers p = t_powers(T9, with_g) the caller supplies
+NB_HD inline void eval_rates(const Net& t, const Zone& s, const WS& w, const TPow& p,
                              double T9, bool with_g) {
-  const TPow p = t_powers(T9, with_g);
   // one warp per scheduler leaves FP64 latency exposed: two reactions per
   // iteration and two partial sums per exponent give independent chains
 #pragma unroll 2
@@ -149,6 +151,32 @@ NB_HD inline void eval_rates(const Net& t, const Zone& s, const WS& w,
     w.k[r] = exp_tang(e) * (rp * t.scale[r]);
     if (with_g) w.g[r] = rate_dlog(a[1], a[2], a[3], a[4], a[5], a[6], p);
   }
+}
+
+// k_r at T9 from the rates kept at the attempt's reference temperature
+// (rate_near); the reference's own k_r are saved by save_ref_rates
+NB_HD inline void eval_rates_near(const Net& t, const Zone& s, const WS& w, double T9,
+                                  const TPow& ref, double T9ref) {
+  const TPow p = t_powers(T9, false);
+  const DPhi d = delta_phi(p, ref, T9, T9ref);
+#pragma unroll 2
+  for (int r = 0; r < t.R; ++r) {
+    const double* a = t.coef + 7 * r;
+    const double de = rate_delta(a[1], a[2], a[3], a[4], a[5], a[6], d);
+    if (small_delta(de)) {
+      w.k[r] = rate_near(w.kp[r], de);
+    } else {
+      double e = rate_exponent(a[0], a[1], a[2], a[3], a[4], a[5], a[6], p, T9);
+      if (s.lnm) e += s.lnm[r];
+      const int nr = t.nrho[r];
+      const double rp = nr == 0 ? 1.0 : (nr == 1 ? s.rho : s.rho2);
+      w.k[r] = exp_tang(e) * (rp * t.scale[r]);
+    }
+  }
+}
+
+NB_HD __forceinline__ void save_ref_rates(const Net& t, const WS& w) {
+  for (int r = 0; r < t.R; ++r) w.kp[r] = w.k[r];
 }
 
 // R_r = k_r prod Y over reactant occurrences, for state v

@@ -9,7 +9,10 @@
 //       eh [HMAX], th [HMAX]; each is indexable with operator[].
 // and calls the network-specific operations by unqualified name, so that the
 // overloads for NT are found at instantiation:
-//   eval_rates(t, s, w, T9, with_g)   k_r (and g_r = d ln lambda_r/dT9)
+//   eval_rates(t, s, w, p, T9, with_g)  k_r (and g_r = d ln lambda_r/dT9),
+//                                     p = t_powers(T9, with_g)
+//   save_ref_rates(t, w)              kp_r = k_r (the reference rates)
+//   eval_rates_near(t, s, w, T9, ref, T9ref)  k_r from kp_r (rate_near)
 //   eval_terms(t, w, v)               rr_r = k_r prod Y of the reactants
 //   eval_f(t, w, v, out)              out = f(v) from rr
 //   eval_edot(t, w)                   sum_r Q_r rr_r
@@ -166,6 +169,54 @@ NB_HD __forceinline__ double rate_dlog(double a1, double a2, double a3, double a
   g2 = fma(a6, p.iT, g2);
   g1 = fma(a3, p.d3, g1);
   return g1 + g2;
+}
+
+// Rates near a reference temperature.  Within one step attempt T9 moves
+// only slightly from the predictor's value T9ref, where every k_r was
+// evaluated in full.  Then k_r(T9) = k_r(T9ref) exp(de_r) with
+// de_r = e_r(T9) - e_r(T9ref) = sum_{i>=1} a_i (phi_i(T9) - phi_i(T9ref));
+// the constant part of the exponent (a0, the multiplier) and the factors
+// rho^(n_r-1) scale_r cancel.  For |de| <= 2^-10, exp(de) - 1 comes from its
+// Taylor polynomial of degree 4 (truncation x^5/120 < 2^-56 relative), and
+// k = kref + kref (exp(de) - 1).  The exponent's absolute rounding error is
+// the same as when it is formed whole, so the rates are as accurate as the
+// full evaluation's.  A larger de takes the full evaluation.
+struct DPhi {
+  double d1, d2, d3, d4, d5, d6;
+};
+
+NB_HD __forceinline__ DPhi delta_phi(const TPow& p, const TPow& r, double T9, double T9r) {
+  DPhi d;
+  d.d1 = p.iT - r.iT;
+  d.d2 = p.it13 - r.it13;
+  d.d3 = p.t13 - r.t13;
+  d.d4 = T9 - T9r;
+  d.d5 = p.T53 - r.T53;
+  d.d6 = p.lnT - r.lnT;
+  return d;
+}
+
+NB_HD __forceinline__ double rate_delta(double a1, double a2, double a3, double a4,
+                                        double a5, double a6, const DPhi& d) {
+  double e1 = a1 * d.d1;
+  double e2 = a4 * d.d4;
+  e1 = fma(a2, d.d2, e1);
+  e2 = fma(a5, d.d5, e2);
+  e1 = fma(a3, d.d3, e1);
+  e2 = fma(a6, d.d6, e2);
+  return e1 + e2;
+}
+
+// |de| <= 2^-10 (and finite), decided on the bits
+NB_HD __forceinline__ bool small_delta(double de) {
+  return (dbits(de) & 0x7fffffffffffffffLL) <= 0x3f50000000000000LL;
+}
+
+NB_HD __forceinline__ double rate_near(double kref, double de) {
+  double q = fma(de, 1.0 / 24.0, 1.0 / 6.0);
+  q = fma(q, de, 0.5);
+  q = fma(q, de, 1.0);
+  return fma(kref, q * de, kref);
 }
 
 // c_v = 1.5 sum_i Y_i + 1e-3 T9^3 (two interleaved partial sums)
@@ -394,7 +445,7 @@ NB_HD __forceinline__ bool zone_init(const NT& t, Zone& s, WT& w, const BurnPara
     P.tape.T9f[z] = s.T9f;
     tape_record(t, P, s, x0, 0.0, 0);
   }
-  eval_rates(t, s, w, s.T9f, false);
+  eval_rates(t, s, w, t_powers(s.T9f, false), s.T9f, false);
   s.c_teval++;
   eval_terms(t, w, x0);
   eval_f(t, w, x0, w.f0);
@@ -420,7 +471,11 @@ NB_HD __forceinline__ bool zone_init(const NT& t, Zone& s, WT& w, const BurnPara
   if (hp > s.tend) hp = s.tend;
   NB_UNROLL
   for (int i = 0; i < n; ++i) w.x[i] = fma(hp, w.f0[i], x0[i]);
-  if (t.sh) { eval_rates(t, s, w, w.x[N], false); s.c_teval++; }
+  if (t.sh) {
+    const double T9 = w.x[N];
+    eval_rates(t, s, w, t_powers(T9, false), T9, false);
+    s.c_teval++;
+  }
   eval_terms(t, w, w.x);
   eval_f(t, w, w.x, w.f);
   s.c_rhs++;
@@ -488,8 +543,17 @@ NB_HD __forceinline__ bool zone_attempt(const NT& t, Zone& s, WT& w, const BurnP
   }
   NB_UNROLL
   for (int i = 0; i < n; ++i) w.x[i] = w.xp[i];
-  // Jacobian at the predictor, M, LU
-  if (t.sh) { eval_rates(t, s, w, w.x[N], true); s.c_teval++; }
+  // Jacobian at the predictor, M, LU; with self-heating the predictor's
+  // temperature is the attempt's reference for the rates
+  TPow pref;
+  double Tref = 0.0;
+  if (t.sh) {
+    Tref = w.x[N];
+    pref = t_powers(Tref, true);
+    eval_rates(t, s, w, pref, Tref, true);
+    save_ref_rates(t, w);
+    s.c_teval++;
+  }
   eval_terms(t, w, w.x);
   assemble_M(t, w, w.x, alpha[0], h);
   s.c_jac++;
@@ -499,7 +563,7 @@ NB_HD __forceinline__ bool zone_attempt(const NT& t, Zone& s, WT& w, const BurnP
   double nrm_prev = 0.0;
   for (int m = 0; ok && m < 4; ++m) {
     if (m > 0) {
-      if (t.sh) { eval_rates(t, s, w, w.x[N], false); s.c_teval++; }
+      if (t.sh) { eval_rates_near(t, s, w, w.x[N], pref, Tref); s.c_teval++; }
       eval_terms(t, w, w.x);
     }
     eval_f(t, w, w.x, w.f);
@@ -549,7 +613,7 @@ NB_HD __forceinline__ bool zone_attempt(const NT& t, Zone& s, WT& w, const BurnP
   // accept
   double E_new = 0.0;
   if (t.hasE) {
-    if (t.sh) { eval_rates(t, s, w, w.x[N], false); s.c_teval++; }
+    if (t.sh) { eval_rates_near(t, s, w, w.x[N], pref, Tref); s.c_teval++; }
     eval_terms(t, w, w.x);
     const double ed = eval_edot(t, w);
     s.c_edot++;

@@ -331,7 +331,7 @@ int build_blob(const nb_topology* T, const double* coeffs,
   // placed in shared memory), then the history and start-up arrays
   h.w_x = take(n); h.w_xp = take(n); h.w_psi = take(n); h.w_d = take(n);
   h.w_f = take(n); h.w_iw = take(n);
-  h.w_k = take(R); h.w_g = take(R); h.w_rr = take(R);
+  h.w_k = take(R); h.w_g = take(R); h.w_rr = take(R); h.w_kp = take(R);
   h.w_dt = take(nd + R);   // [dterms | R_r g_r]
   h.w_lu = take(nnz);
   h.hot_doubles = w;
