@@ -253,6 +253,38 @@ int nb_burn_batch_noalloc(nb_net net, int64_t Z, const double* Y0,
                           double* E, int32_t* counters, int32_t* status,
                           const nb_options* opt, void* stream);
 
+/* Several networks in one launch.  The paper's study burns the same hydro
+ * zones with different networks to see which nuclear physics matters
+ * (Sec. 3, 4).  nb_burn_multi burns up to NB_MULTI_MAX_SETS sets, each a
+ * network with its own zones and arrays (as for nb_burn_batch, device
+ * pointers, [Z, N] with that network's N), in one persistent launch whose
+ * device queue spans all of them: a few expensive zones of a large network
+ * and many cheap zones of a small one share the GPU's lanes.  Sets of larger
+ * networks are claimed first.  Every zone follows the generic kernel, bit
+ * for bit the result nb_burn_batch gives it.  t_end, rtol and atol are
+ * common; t_end_zone (per set, may be NULL) overrides t_end per zone.  From
+ * opt: max_attempts, threads_per_block (<= 128), blocks_per_sm and
+ * time_budget_s; no tape, no specialised kernel.  All networks must live on
+ * the current device.  The first set's network lends its device workspace:
+ * do not burn with it concurrently.  Asynchronous on stream. */
+#define NB_MULTI_MAX_SETS 12
+typedef struct {
+  nb_net net;
+  int64_t Z;
+  const double* Y0;         /* [Z, N] */
+  const double* T9_0;       /* [Z] */
+  const double* rho;        /* [Z] */
+  const double* ln_mult;    /* NULL, [R] or [Z, R] */
+  int32_t ln_mult_per_zone;
+  const double* t_end_zone; /* [Z] or NULL */
+  double* Y;                /* [Z, N] out */
+  double* T9;               /* [Z] out */
+  double* E;                /* [Z] out or NULL */
+  int32_t* counters;        /* [Z, NB_NCOUNT] out or NULL */
+  int32_t* status;          /* [Z] out */
+} nb_burn_set;
+int nb_burn_multi(int32_t n_sets, const nb_burn_set* sets, double t_end, double rtol,
+                  double atol, const nb_options* opt, void* stream);
 /* Network-specialised kernel.  The paper's pynucastro writes each network
  * as its own code, every rate, RHS term and Jacobian entry spelled out
  * (Sec. 2).  The generic kernel instead walks the compiled network from

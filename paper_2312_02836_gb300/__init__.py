@@ -20,7 +20,7 @@ from . import _abi
 from ._abi import (COUNTER_NAMES, KERNEL_PERSISTENT, KERNEL_PLAIN, NCOUNT,
                    ZONE_STATUS, NetburnError)
 
-__all__ = ["Network", "specialized_source", "specialize_compile", "burn", "burn_host", "BurnGraph", "Tape", "adjoint", "Burn",
+__all__ = ["Network", "specialized_source", "specialize_compile", "burn", "burn_multi", "burn_host", "BurnGraph", "Tape", "adjoint", "Burn",
            "BurnResult", "NetburnError", "COUNTER_NAMES", "ZONE_STATUS",
            "KERNEL_PERSISTENT", "KERNEL_PLAIN", "library_path", "probe_fp64"]
 
@@ -222,6 +222,58 @@ def burn(net: Network, Y0, T9, rho, t_end: float, rtol: float, atol: float,
     if tape is not None:
         tape._recorded(Z, ln_mult, float(t_end), float(rtol), float(atol))
     return out
+
+
+def burn_multi(sets, t_end: float, rtol: float, atol: float, *, threads_per_block=0,
+               blocks_per_sm=0, max_attempts=500000, time_budget_s=0.0, stream=None):
+    """Burn several networks' zones in one launch (``nb_burn_multi``).
+
+    ``sets``: a list of dicts with keys net, Y0, T9, rho and optionally
+    ln_mult ([R] or [Z, R]) and t_end (a CUDA float64 tensor [Z] of per-zone
+    end times); tensors as for ``burn``.  Returns one BurnResult per set."""
+    torch = _torch()
+    if not 1 <= len(sets) <= _abi.MULTI_MAX_SETS:
+        raise NetburnError(f"1..{_abi.MULTI_MAX_SETS} sets")
+    arr = (_abi.BurnSet * len(sets))()
+    outs = []
+    ptr = lambda t: None if t is None else t.data_ptr()
+    for b, d in zip(arr, sets):
+        net = d["net"]
+        Y0, T9, rho = d["Y0"], d["T9"], d["rho"]
+        Z = int(Y0.shape[0])
+        _dev(Y0, torch, "Y0", (Z, net.N))
+        _dev(T9, torch, "T9", (Z,))
+        _dev(rho, torch, "rho", (Z,))
+        lm = d.get("ln_mult")
+        per_zone = 0
+        if lm is not None:
+            _dev(lm, torch, "ln_mult")
+            per_zone = 1 if lm.dim() == 2 else 0
+            if tuple(lm.shape) not in ((net.R,), (Z, net.R)):
+                raise NetburnError("ln_mult must be [R] or [Z, R]")
+        tz = d.get("t_end")
+        if tz is not None:
+            _dev(tz, torch, "t_end", (Z,))
+        dev = Y0.device
+        out = BurnResult(torch.empty((Z, net.N), dtype=torch.float64, device=dev),
+                         torch.empty((Z,), dtype=torch.float64, device=dev),
+                         torch.empty((Z,), dtype=torch.float64, device=dev),
+                         torch.empty((Z, NCOUNT), dtype=torch.int32, device=dev),
+                         torch.empty((Z,), dtype=torch.int32, device=dev))
+        outs.append(out)
+        b.net = net.handle.value
+        b.Z = Z
+        b.Y0, b.T9_0, b.rho = ptr(Y0), ptr(T9), ptr(rho)
+        b.ln_mult, b.ln_mult_per_zone, b.t_end_zone = ptr(lm), per_zone, ptr(tz)
+        b.Y, b.T9, b.E = ptr(out.Y), ptr(out.T9), ptr(out.E)
+        b.counters, b.status = ptr(out.counters), ptr(out.status)
+    o = _options("persistent", threads_per_block, blocks_per_sm, -1, max_attempts,
+                 time_budget_s=time_budget_s)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    rc = _abi.load().nb_burn_multi(len(sets), arr, float(t_end), float(rtol), float(atol),
+                                   C.byref(o), C.c_void_p(st.cuda_stream))
+    _abi.check(rc, "nb_burn_multi")
+    return outs
 
 
 class BurnGraph:

@@ -25,7 +25,8 @@ KERNEL_PLAIN = 1
 EXPORTS = ("nb_net_load", "nb_net_free", "nb_net_get_info", "nb_default_options",
            "nb_burn_batch", "nb_burn_batch_host", "nb_tape_alloc", "nb_tape_free",
            "nb_tape_steps", "nb_burn_adjoint", "nb_burn_batch_noalloc",
-           "nb_net_specialize", "nb_specialize_source", "nb_specialize_compile",
+           "nb_burn_multi", "nb_net_specialize", "nb_specialize_source",
+           "nb_specialize_compile",
            "nb_exp_eval", "nb_probe_fp64", "nb_strerror")
 
 
@@ -48,6 +49,17 @@ class NetInfo(C.Structure):
                 ("flops_tsolve", C.c_int64),
                 ("exp_per_rate_eval", C.c_int32), ("specialize_auto", C.c_int32),
                 ("last_specialized", C.c_int32), ("reserved", C.c_int32)]
+
+
+MULTI_MAX_SETS = 12
+
+
+class BurnSet(C.Structure):
+    _fields_ = [("net", C.c_void_p), ("Z", C.c_int64), ("Y0", C.c_void_p),
+                ("T9_0", C.c_void_p), ("rho", C.c_void_p), ("ln_mult", C.c_void_p),
+                ("ln_mult_per_zone", C.c_int32), ("t_end_zone", C.c_void_p),
+                ("Y", C.c_void_p), ("T9", C.c_void_p), ("E", C.c_void_p),
+                ("counters", C.c_void_p), ("status", C.c_void_p)]
 
 
 class Options(C.Structure):
@@ -83,6 +95,8 @@ def load(build_if_needed: bool = True):
         lib.nb_burn_batch_noalloc.argtypes = [P, I64, P, P, P, D, D, D, P, I32, P,
                                               P, P, P, P, P, P]
         lib.nb_burn_batch_noalloc.restype = C.c_int
+        lib.nb_burn_multi.argtypes = [I32, P, D, D, D, P, P]
+        lib.nb_burn_multi.restype = C.c_int
         lib.nb_net_specialize.argtypes = [P, I32, P, I64]
         lib.nb_net_specialize.restype = C.c_int
         lib.nb_specialize_source.argtypes = [P, P, I32, P, I64, P]

@@ -19,8 +19,13 @@ def test_source_spells_out_the_network():
     assert "storage variant 2" in head        # 7n + LU slots > 160: LU in memory
     # one exponent, one rate and one derivative factor per reaction, with the
     # fit coefficients as exact hexadecimal literals
-    assert len(re.findall(r"e = rate_exponent\(", src)) == net.R
-    assert len(re.findall(r"w\.k\[\d+\] = exp_tang\(e\)", src)) == net.R
+    assert len(re.findall(r"^  e = rate_exponent\(", src, re.M)) == net.R
+    # the rates near the attempt's reference temperature: one small-delta
+    # update per reaction, with the full exponent as its fallback
+    assert len(re.findall(r"rate_near\(w\.kp\[\d+\], de\)", src)) == net.R
+    assert len(re.findall(r"^    e = rate_exponent\(", src, re.M)) == net.R
+    assert len(re.findall(r"^  w\.k\[\d+\] = exp_tang\(e\)", src, re.M)) == net.R
+    assert len(re.findall(r"^    w\.k\[\d+\] = exp_tang\(e\)", src, re.M)) == net.R
     assert len(re.findall(r"w\.g\[\d+\] = rate_dlog\(", src)) == net.R
     a = net.coeffs[5]
     assert float.hex(float(a[0])).replace("0x", "") in src.replace("0x", "")

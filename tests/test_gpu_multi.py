@@ -1,0 +1,76 @@
+"""Several networks in one launch (nb_burn_multi): every set's zones must
+come out bit for bit as a single-network burn of the same zones gives them
+(the generic kernel, and so the specialised one too), whatever sets share
+the launch.  Parity of those burns with the oracle is the parity tests'."""
+import numpy as np
+import pytest
+
+import gen
+
+pytestmark = pytest.mark.gpu
+
+
+def _mods():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_2312_02836_gb300 as nb
+    return nb, torch
+
+
+def _set(nb, torch, name, Z, **extra):
+    net, z, s = gen.problem(name, Z)
+    t = {k: torch.from_numpy(v).cuda() for k, v in z.items()}
+    d = dict(net=nb.Network(net), Y0=t["Y"], T9=t["T9"], rho=t["rho"], **extra)
+    return d, net, s
+
+
+def _equal(a, b):
+    import torch
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+
+
+def test_multi_network_batch_equals_single_burns():
+    nb, torch = _mods()
+    sets, specs = [], []
+    for name, Z in (("chain13_heat", 1024), ("net48", 96), ("chain13", 512),
+                    ("chain13_literal", 200)):
+        d, net, s = _set(nb, torch, name, Z)
+        sets.append(d)
+        specs.append(s)
+    # every workload here shares t_end, rtol, atol except net48 (t_end 1e-2):
+    # burn the whole batch at one t_end, overriding net48's per zone
+    s0 = specs[0]
+    tz = torch.full((96,), specs[1]["t_end"], dtype=torch.float64, device="cuda")
+    sets[1]["t_end"] = tz
+    outs = nb.burn_multi(sets, s0["t_end"], s0["rtol"], s0["atol"])
+    torch.cuda.synchronize()
+    for d, s, out in zip(sets, specs, outs):
+        te = d.get("t_end", s0["t_end"])
+        ref = nb.burn(d["net"], d["Y0"], d["T9"], d["rho"], te, s0["rtol"], s0["atol"],
+                      specialize="generic")
+        torch.cuda.synchronize()
+        assert int((out.status == 0).sum()) == d["Y0"].shape[0]
+        _equal(out, ref)
+
+
+def test_multi_network_options_and_empty_set():
+    nb, torch = _mods()
+    a, _, s = _set(nb, torch, "chain13_heat", 300)
+    b, net_b, _ = _set(nb, torch, "chain13", 0)
+    rng = np.random.default_rng(3)
+    lm = torch.from_numpy(rng.normal(0.0, 0.2, (300, a["net"].R))).cuda()
+    a["ln_mult"] = lm
+    outs = nb.burn_multi([b, a], s["t_end"], s["rtol"], s["atol"], threads_per_block=64,
+                         blocks_per_sm=2)
+    torch.cuda.synchronize()
+    assert outs[0].Y.shape[0] == 0
+    ref = nb.burn(a["net"], a["Y0"], a["T9"], a["rho"], s["t_end"], s["rtol"], s["atol"],
+                  lm, specialize="generic")
+    torch.cuda.synchronize()
+    _equal(outs[1], ref)
+    # argument errors are caught on the host
+    with pytest.raises(nb.NetburnError):
+        nb.burn_multi([a] * 13, s["t_end"], s["rtol"], s["atol"])
+    with pytest.raises(nb.NetburnError):
+        nb.burn_multi([a], s["t_end"], -1.0, s["atol"])
