@@ -48,6 +48,14 @@ CONFIGS = {
     "chain13_heat": dict(kind="chain", literal=False, heat=True, Z=65536,
                          T9=(0.5, 5.0), rho=(1e5, 1e8), t_end=1e-3,
                          rtol=1e-8, atol=1e-12, zone_seed=1001, Q=True),
+    # The self-heating chain with its captures on species 1..11 taken as
+    # effective (alpha,p)(p,gamma) rates (the aprox-style approximation of
+    # the paper's Sec. 2): each such rate combines four fits.  Same zones as
+    # chain13_heat.
+    "chain13_heat_ap": dict(kind="chain", literal=False, heat=True, Z=65536,
+                            T9=(0.5, 5.0), rho=(1e5, 1e8), t_end=1e-3,
+                            rtol=1e-8, atol=1e-12, zone_seed=1001, Q=True,
+                            ap_from=1),
     # Random sparse network, 48 species / 180 rates, fixed T and rho.
     "net48": dict(kind="random", N=48, mix=(60, 100, 20), topo_seed=2,
                   heat=False, Z=262144, T9=(0.3, 6.0), rho=(1e4, 1e9),
@@ -81,6 +89,10 @@ class NetworkSpec:
     scale: Optional[np.ndarray] = None  # float64 [R] constant factor, or None
     self_heating: bool = False
     seed_used: int = 0
+    # (alpha,p)(p,gamma) effective rates: ap_pg [R] int8 (1 = effective),
+    # ap_coeffs [R, 3, 7] fits of the (a,p), (p,g) and (p,a) channels
+    ap_pg: Optional[np.ndarray] = None
+    ap_coeffs: Optional[np.ndarray] = None
     extra: dict = field(default_factory=dict)
 
 
@@ -200,9 +212,21 @@ def network(name: str) -> NetworkSpec:
         Q = None
         if cfg["Q"]:
             Q = np.random.Generator(np.random.PCG64(1)).uniform(1.0, 10.0, R)
+        ap_pg = ap_coeffs = None
+        if cfg.get("ap_from") is not None:
+            # reaction r (r >= 1) captures an alpha on species r
+            ap_pg = np.zeros(R, dtype=np.int8)
+            ap_pg[cfg["ap_from"]:] = 1
+            rng = np.random.Generator(np.random.PCG64(5))
+            ap_coeffs = np.zeros((R, 3, 7), dtype=np.float64)
+            for c, shift in enumerate((0.0, 4.0, 0.0)):   # (a,p), (p,g), (p,a)
+                f = _draw_coeffs(rng, R)
+                f[:, 0] += shift            # proton capture faster than (a,p)
+                ap_coeffs[:, c, :] = f
         return NetworkSpec(name=name, N=13, R=R, reactants=reac, products=prod,
                            A=ALPHA_CHAIN_A.copy(), coeffs=coeffs, Q=Q,
-                           self_heating=cfg["heat"], seed_used=0)
+                           self_heating=cfg["heat"], seed_used=0,
+                           ap_pg=ap_pg, ap_coeffs=ap_coeffs)
     N = cfg["N"]
     seed = cfg["topo_seed"]
     while True:

@@ -90,6 +90,16 @@ typedef struct {
   const double* Q;          /* [R] energy per reaction, or NULL (no E) */
   const double* scale;      /* [R] constant factor scale_r, or NULL (= 1) */
   int32_t self_heating;     /* 1: T9 is integrated (requires Q) */
+  /* (alpha,p)(p,gamma) effective rates (Sec. 2: A(a,p)X(p,g)B taken as one
+   * A(a,g)B rate when proton capture on X is fast and the proton flow
+   * through X is in equilibrium).  ap_pg [R] or NULL: 1 marks reaction r as
+   * effective, 0 a plain fit.  ap_coeffs [R, 3, 7] (required with ap_pg):
+   * the fits of the (a,p), (p,g) and (p,a) channels; coeffs[r] is then the
+   * direct (a,g) channel.  X in steady state gives
+   *   lambda_r = lambda_ag + lambda_ap lambda_pg / (lambda_pg + lambda_pa),
+   * and the multiplier p_r scales the whole effective rate. */
+  const int8_t* ap_pg;
+  const double* ap_coeffs;
 } nb_topology;
 
 typedef struct {

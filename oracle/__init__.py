@@ -50,7 +50,8 @@ def build(force: bool = False) -> str:
 class _Net(C.Structure):
     _fields_ = [("N", C.c_int32), ("R", C.c_int32), ("self_heating", C.c_int32),
                 ("reactants", C.c_void_p), ("products", C.c_void_p),
-                ("Q", C.c_void_p), ("scale", C.c_void_p), ("coeffs", C.c_void_p)]
+                ("Q", C.c_void_p), ("scale", C.c_void_p), ("coeffs", C.c_void_p),
+                ("ap_pg", C.c_void_p), ("ap_coeffs", C.c_void_p)]
 
 
 class _Opt(C.Structure):
@@ -106,12 +107,19 @@ class Network:
         self.coeffs = _f64(spec.coeffs)
         self.Q = _f64(getattr(spec, "Q", None))
         self.scale = _f64(getattr(spec, "scale", None))
+        ap = getattr(spec, "ap_pg", None)
+        self.ap_pg = None if ap is None else np.ascontiguousarray(ap, dtype=np.int8)
+        self.ap_coeffs = _f64(getattr(spec, "ap_coeffs", None))
+        if self.ap_pg is not None and (self.ap_coeffs is None
+                                       or self.ap_coeffs.size != 21 * self.R):
+            raise ValueError("ap_pg needs ap_coeffs [R, 3, 7]")
         if self.self_heating and self.Q is None:
             raise ValueError("self-heating needs Q")
         self.n = self.N + (1 if self.self_heating else 0)
         self._s = _Net(self.N, self.R, int(self.self_heating),
                        _p(self.reactants), _p(self.products), _p(self.Q),
-                       _p(self.scale), _p(self.coeffs))
+                       _p(self.scale), _p(self.coeffs), _p(self.ap_pg),
+                       _p(self.ap_coeffs))
 
     @property
     def ptr(self):

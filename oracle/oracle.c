@@ -18,6 +18,15 @@
  *   RHS         dY_i/dt = sum_r c_ir R_r,  c_ir = #(i in products) - #(i in reactants)
  *   energy      edot = sum_r Q_r R_r,  dE/dt = edot
  *   heating     dT9/dt = edot / c_v,  c_v = 1.5 sum_i Y_i + 1e-3 T9^3
+ *   effective   a reaction flagged as the (alpha,p)(p,gamma) approximation of
+ *               Sec. 2 (A(a,p)X(p,g)B merged into one A(a,g)B rate, valid
+ *               when proton capture on X is fast, so that the proton flow
+ *               through X is in equilibrium) uses
+ *               lambda = lambda_ag + lambda_ap lambda_pg / (lambda_pg + lambda_pa):
+ *               X in steady state, d(Y_X Y_p)/dt = 0, splits the flow from
+ *               A(a,p)X between X(p,g)B and the return X(p,a)A.  Each of the
+ *               four lambdas is a 7-parameter fit; the paper states the
+ *               approximation in words only, this is its first-principles form
  *
  * The integrator is variable-step, variable-order (1..5) BDF in Lagrange
  * (variable-coefficient) form with a modified Newton iteration, as in the
@@ -84,6 +93,8 @@ typedef struct {
     const double* Q;            /* [R] or NULL */
     const double* scale;        /* [R] or NULL (1) */
     const double* coeffs;       /* [R*7] */
+    const int8_t* ap_pg;        /* [R] or NULL: 1 = (alpha,p)(p,gamma) effective */
+    const double* ap_coeffs;    /* [R*21] fits of (a,p), (p,g), (p,a), or NULL */
 } ora_network;
 
 typedef struct {
@@ -139,7 +150,27 @@ void ora_rate_factors(const ora_network* net, double T9, double rho,
         double p = ln_mult ? ln_mult[r] : 0.0;
         double rp = 1.0;
         for (int m = 1; m < n_reactants(net, r); ++m) rp *= rho;
-        k[r] = s * exp(p) * rp * exp(e);
+        double lam = exp(e);
+        if (net->ap_pg && net->ap_pg[r]) {
+            /* lambda = lambda_ag + lambda_ap lambda_pg / (lambda_pg + lambda_pa) */
+            double ec[3], dec[3];
+            for (int c = 0; c < 3; ++c) {
+                const double* b = net->ap_coeffs + 21 * r + 7 * c;
+                ec[c] = 0.0;
+                dec[c] = 0.0;
+                for (int j = 0; j < 7; ++j) {
+                    ec[c] += b[j] * phi[j];
+                    dec[c] += b[j] * dphi[j];
+                }
+            }
+            double l_ag = lam, l_ap = exp(ec[0]), l_pg = exp(ec[1]), l_pa = exp(ec[2]);
+            double frac = l_pg / (l_pg + l_pa);
+            double via_p = l_ap * frac;
+            lam = l_ag + via_p;
+            /* d ln lambda / dT9: d frac/dT9 = frac (1 - frac) (g_pg - g_pa) */
+            de = (l_ag * de + via_p * (dec[0] + (1.0 - frac) * (dec[1] - dec[2]))) / lam;
+        }
+        k[r] = s * exp(p) * rp * lam;
         if (g) g[r] = de;
     }
 }

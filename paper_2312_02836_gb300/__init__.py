@@ -46,10 +46,13 @@ def _topology(spec):
     arrays = dict(reac=_np(spec.reactants, np.int16), prod=_np(spec.products, np.int16),
                   coef=_np(spec.coeffs, np.float64),
                   Q=_np(getattr(spec, "Q", None), np.float64),
-                  scale=_np(getattr(spec, "scale", None), np.float64))
+                  scale=_np(getattr(spec, "scale", None), np.float64),
+                  ap_pg=_np(getattr(spec, "ap_pg", None), np.int8),
+                  ap_coeffs=_np(getattr(spec, "ap_coeffs", None), np.float64))
     p = lambda a: None if a is None else a.ctypes.data
     topo = _abi.Topology(int(spec.N), int(spec.R), p(arrays["reac"]), p(arrays["prod"]),
-                         p(arrays["Q"]), p(arrays["scale"]), int(bool(spec.self_heating)))
+                         p(arrays["Q"]), p(arrays["scale"]), int(bool(spec.self_heating)),
+                         p(arrays["ap_pg"]), p(arrays["ap_coeffs"]))
     return arrays, topo, p(arrays["coef"])
 
 

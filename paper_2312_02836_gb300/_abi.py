@@ -34,7 +34,8 @@ class Topology(C.Structure):
     _fields_ = [("n_species", C.c_int32), ("n_reactions", C.c_int32),
                 ("reactants", C.c_void_p), ("products", C.c_void_p),
                 ("Q", C.c_void_p), ("scale", C.c_void_p),
-                ("self_heating", C.c_int32)]
+                ("self_heating", C.c_int32), ("ap_pg", C.c_void_p),
+                ("ap_coeffs", C.c_void_p)]
 
 
 class NetInfo(C.Structure):

@@ -82,7 +82,9 @@ struct BlobHeader {
   int32_t n_exp_per_teval;
   int32_t hot_doubles;  // leading part of the per-lane layout kept hot
   int32_t w_kp;         // k_r at the step's reference temperature (self-heating)
-  int32_t pad_;
+  int32_t o_ap;         // int32 [R] row of the effective-rate fits, -1 = plain
+  int32_t o_apc;        // double [n_ap * 21] (a,p), (p,g), (p,a) fits
+  int32_t n_ap;         // effective (alpha,p)(p,gamma) rates
 };
 
 }  // namespace nb

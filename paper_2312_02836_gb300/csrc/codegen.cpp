@@ -154,24 +154,45 @@ std::string specialized_source(const std::vector<uint8_t>& blob, int variant) {
   o("  LV f0, xh, eh, th;\n};\n\n");
 
   // ---- rates
+  const int32_t* ap = arr<int32_t>(blob, h.o_ap);
+  const double* apc = arr<double>(blob, h.o_apc);
+  auto fit7 = [&](const double* a, int from) {
+    std::string t;
+    for (int j = from; j < 7; ++j) t += (j > from ? ", " : "") + lit(a[j]);
+    return t;
+  };
+  // the full evaluation of k_r (and g_r when `g`), in the generic kernel's
+  // order (rate_full)
+  auto emit_full = [&](int r, const char* ind, bool g) {
+    const double* a = coef + 7 * r;
+    const char* rp = nrho[r] == 0 ? "1.0" : (nrho[r] == 1 ? "s.rho" : "s.rho2");
+    o("%se = rate_exponent(%s, p, T9);\n", ind, fit7(a, 0).c_str());
+    o("%sif (lnm) e += lnm[%d];\n", ind, r);
+    if (ap[r] < 0) {
+      o("%sw.k[%d] = exp_tang(e) * (%s * %s);\n", ind, r, rp, lit(scale[r]).c_str());
+      if (g) o("%sif (with_g) w.g[%d] = rate_dlog(%s, p);\n", ind, r, fit7(a, 1).c_str());
+      return;
+    }
+    const double* b = apc + 21 * ap[r];
+    o("%s{\n%s  double eap = rate_exponent(%s, p, T9);\n", ind, ind, fit7(b, 0).c_str());
+    o("%s  if (lnm) eap += lnm[%d];\n", ind, r);
+    o("%s  const double epg = rate_exponent(%s, p, T9);\n", ind, fit7(b + 7, 0).c_str());
+    o("%s  const double epa = rate_exponent(%s, p, T9);\n", ind, fit7(b + 14, 0).c_str());
+    o("%s  const APRate q = ap_rate(e, eap, epg, epa);\n", ind);
+    if (g)
+      o("%s  if (with_g)\n%s    w.g[%d] = ap_dlog(q, rate_dlog(%s, p), rate_dlog(%s, p),\n"
+        "%s                     rate_dlog(%s, p), rate_dlog(%s, p));\n",
+        ind, ind, r, fit7(a, 1).c_str(), fit7(b, 1).c_str(), ind, fit7(b + 7, 1).c_str(),
+        fit7(b + 14, 1).c_str());
+    o("%s  w.k[%d] = q.lam * (%s * %s);\n%s}\n", ind, r, rp, lit(scale[r]).c_str(), ind);
+  };
   o("NB_HD __forceinline__ void eval_rates(const GNet&, const Zone& s, GWS& w, const TPow& p,"
     " double T9, bool with_g) {\n  const double* lnm = s.lnm;\n  double e;\n");
-  for (int r = 0; r < R; ++r) {
-    const double* a = coef + 7 * r;
-    o("  e = rate_exponent(%s, %s, %s, %s, %s, %s, %s, p, T9);\n", lit(a[0]).c_str(),
-      lit(a[1]).c_str(), lit(a[2]).c_str(), lit(a[3]).c_str(), lit(a[4]).c_str(),
-      lit(a[5]).c_str(), lit(a[6]).c_str());
-    o("  if (lnm) e += lnm[%d];\n", r);
-    const char* rp = nrho[r] == 0 ? "1.0" : (nrho[r] == 1 ? "s.rho" : "s.rho2");
-    o("  w.k[%d] = exp_tang(e) * (%s * %s);\n", r, rp, lit(scale[r]).c_str());
-    if (sh)
-      o("  if (with_g) w.g[%d] = rate_dlog(%s, %s, %s, %s, %s, %s, p);\n", r,
-        lit(a[1]).c_str(), lit(a[2]).c_str(), lit(a[3]).c_str(), lit(a[4]).c_str(),
-        lit(a[5]).c_str(), lit(a[6]).c_str());
-  }
+  for (int r = 0; r < R; ++r) emit_full(r, "  ", sh);
   o("}\n\n");
 
-  // ---- rates near the attempt's reference temperature (self-heating)
+  // ---- rates near the attempt's reference temperature (self-heating);
+  // effective (alpha,p)(p,gamma) rates always take the full evaluation
   o("NB_HD __forceinline__ void save_ref_rates(const GNet&, GWS& w) {\n");
   if (sh)
     for (int r = 0; r < R; ++r) o("  w.kp[%d] = w.k[%d];\n", r, r);
@@ -182,16 +203,14 @@ std::string specialized_source(const std::vector<uint8_t>& blob, int variant) {
     o("  const TPow p = t_powers(T9, false);\n  const DPhi d = delta_phi(p, ref, T9, T9ref);\n"
       "  const double* lnm = s.lnm;\n  double de, e;\n");
     for (int r = 0; r < R; ++r) {
-      const double* a = coef + 7 * r;
-      o("  de = rate_delta(%s, %s, %s, %s, %s, %s, d);\n", lit(a[1]).c_str(), lit(a[2]).c_str(),
-        lit(a[3]).c_str(), lit(a[4]).c_str(), lit(a[5]).c_str(), lit(a[6]).c_str());
+      if (ap[r] >= 0) {
+        emit_full(r, "  ", false);
+        continue;
+      }
+      o("  de = rate_delta(%s, d);\n", fit7(coef + 7 * r, 1).c_str());
       o("  if (small_delta(de)) {\n    w.k[%d] = rate_near(w.kp[%d], de);\n  } else {\n", r, r);
-      o("    e = rate_exponent(%s, %s, %s, %s, %s, %s, %s, p, T9);\n", lit(a[0]).c_str(),
-        lit(a[1]).c_str(), lit(a[2]).c_str(), lit(a[3]).c_str(), lit(a[4]).c_str(),
-        lit(a[5]).c_str(), lit(a[6]).c_str());
-      o("    if (lnm) e += lnm[%d];\n", r);
-      const char* rp = nrho[r] == 0 ? "1.0" : (nrho[r] == 1 ? "s.rho" : "s.rho2");
-      o("    w.k[%d] = exp_tang(e) * (%s * %s);\n  }\n", r, rp, lit(scale[r]).c_str());
+      emit_full(r, "    ", false);
+      o("  }\n");
     }
   }
   o("}\n\n");

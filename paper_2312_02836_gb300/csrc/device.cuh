@@ -30,8 +30,8 @@ namespace nb {
 struct Net {
   int n, N, R, sh, hasE, nnz, nd;
   double inv_n;
-  const double *coef, *Q, *scale, *rhs_c, *dt_m, *js_c, *rg_c;
-  const int32_t *nrho, *nreac, *rhs_ptr, *js_ptr, *diag_orig, *rg_ptr;
+  const double *coef, *Q, *scale, *rhs_c, *dt_m, *js_c, *rg_c, *apc;
+  const int32_t *nrho, *nreac, *rhs_ptr, *js_ptr, *diag_orig, *rg_ptr, *ap;
   const int16_t *reac, *rhs_r, *dt_r, *dt_o, *dt_j, *js_src, *lslot, *uslot, *dslot;
   const int16_t *fw_s, *fw_c, *bw_s, *bw_c, *tfw_s, *tfw_c, *tbw_s, *tbw_c, *rg_i;
   const uint8_t* js_flag;
@@ -56,6 +56,7 @@ NB_HD inline Net make_net(const unsigned char* b) {
   t.scale = at<double>(b, h->o_scale); t.rhs_c = at<double>(b, h->o_rhs_c);
   t.dt_m = at<double>(b, h->o_dt_m); t.js_c = at<double>(b, h->o_js_c);
   t.rg_c = at<double>(b, h->o_rg_c);
+  t.apc = at<double>(b, h->o_apc); t.ap = at<int32_t>(b, h->o_ap);
   t.nrho = at<int32_t>(b, h->o_nrho); t.nreac = at<int32_t>(b, h->o_nreac);
   t.rhs_ptr = at<int32_t>(b, h->o_rhs_ptr); t.js_ptr = at<int32_t>(b, h->o_js_ptr);
   t.diag_orig = at<int32_t>(b, h->o_diag_orig); t.rg_ptr = at<int32_t>(b, h->o_rg_ptr);
@@ -135,6 +136,33 @@ NB_HD __forceinline__ WS make_ws(const Net& t, double* lane_base) {
 
 // ---------------------------------------------------------------- model
 
+// k_r of reaction r (and g_r = d ln lambda_r / dT9 when g) at T9 with powers p
+NB_HD __forceinline__ double rate_full(const Net& t, const Zone& s, int r, const TPow& p,
+                                       double T9, double* g) {
+  const double* a = t.coef + 7 * r;
+  double e = rate_exponent(a[0], a[1], a[2], a[3], a[4], a[5], a[6], p, T9);
+  if (s.lnm) e += s.lnm[r];
+  const int nr = t.nrho[r];
+  const double rp = nr == 0 ? 1.0 : (nr == 1 ? s.rho : s.rho2);
+  const int api = t.ap[r];
+  if (api < 0) {
+    if (g) *g = rate_dlog(a[1], a[2], a[3], a[4], a[5], a[6], p);
+    return exp_tang(e) * (rp * t.scale[r]);
+  }
+  const double* b = t.apc + 21 * api;
+  double eap = rate_exponent(b[0], b[1], b[2], b[3], b[4], b[5], b[6], p, T9);
+  if (s.lnm) eap += s.lnm[r];
+  const double epg = rate_exponent(b[7], b[8], b[9], b[10], b[11], b[12], b[13], p, T9);
+  const double epa = rate_exponent(b[14], b[15], b[16], b[17], b[18], b[19], b[20], p, T9);
+  const APRate q = ap_rate(e, eap, epg, epa);
+  if (g)
+    *g = ap_dlog(q, rate_dlog(a[1], a[2], a[3], a[4], a[5], a[6], p),
+                 rate_dlog(b[1], b[2], b[3], b[4], b[5], b[6], p),
+                 rate_dlog(b[8], b[9], b[10], b[11], b[12], b[13], p),
+                 rate_dlog(b[15], b[16], b[17], b[18], b[19], b[20], p));
+  return q.lam * (rp * t.scale[r]);
+}
+
 // k_r (and g_r = d ln lambda_r / dT9 when with_g) for temperature T9, whose
 // powers p = t_powers(T9, with_g) the caller supplies
 NB_HD inline void eval_rates(const Net& t, const Zone& s, const WS& w, const TPow& p,
@@ -143,18 +171,15 @@ NB_HD inline void eval_rates(const Net& t, const Zone& s, const WS& w, const TPo
   // iteration and two partial sums per exponent give independent chains
 #pragma unroll 2
   for (int r = 0; r < t.R; ++r) {
-    const double* a = t.coef + 7 * r;
-    double e = rate_exponent(a[0], a[1], a[2], a[3], a[4], a[5], a[6], p, T9);
-    if (s.lnm) e += s.lnm[r];
-    const int nr = t.nrho[r];
-    const double rp = nr == 0 ? 1.0 : (nr == 1 ? s.rho : s.rho2);
-    w.k[r] = exp_tang(e) * (rp * t.scale[r]);
-    if (with_g) w.g[r] = rate_dlog(a[1], a[2], a[3], a[4], a[5], a[6], p);
+    double g;
+    w.k[r] = rate_full(t, s, r, p, T9, with_g ? &g : nullptr);
+    if (with_g) w.g[r] = g;
   }
 }
 
 // k_r at T9 from the rates kept at the attempt's reference temperature
-// (rate_near); the reference's own k_r are saved by save_ref_rates
+// (rate_near); the reference's own k_r are saved by save_ref_rates.
+// Effective (alpha,p)(p,gamma) rates always take the full evaluation.
 NB_HD inline void eval_rates_near(const Net& t, const Zone& s, const WS& w, double T9,
                                   const TPow& ref, double T9ref) {
   const TPow p = t_powers(T9, false);
@@ -163,15 +188,8 @@ NB_HD inline void eval_rates_near(const Net& t, const Zone& s, const WS& w, doub
   for (int r = 0; r < t.R; ++r) {
     const double* a = t.coef + 7 * r;
     const double de = rate_delta(a[1], a[2], a[3], a[4], a[5], a[6], d);
-    if (small_delta(de)) {
-      w.k[r] = rate_near(w.kp[r], de);
-    } else {
-      double e = rate_exponent(a[0], a[1], a[2], a[3], a[4], a[5], a[6], p, T9);
-      if (s.lnm) e += s.lnm[r];
-      const int nr = t.nrho[r];
-      const double rp = nr == 0 ? 1.0 : (nr == 1 ? s.rho : s.rho2);
-      w.k[r] = exp_tang(e) * (rp * t.scale[r]);
-    }
+    if (t.ap[r] < 0 && small_delta(de)) w.k[r] = rate_near(w.kp[r], de);
+    else w.k[r] = rate_full(t, s, r, p, T9, nullptr);
   }
 }
 

@@ -171,6 +171,32 @@ NB_HD __forceinline__ double rate_dlog(double a1, double a2, double a3, double a
   return g1 + g2;
 }
 
+// Effective (alpha,p)(p,gamma) rate from the exponents of its four channels
+// (the multiplier already added to the direct and (a,p) ones):
+// lambda = l_ag + l_ap frac, frac = l_pg / (l_pg + l_pa), here written
+// 1 / (1 + exp(e_pa - e_pg)) so that it stays defined when both proton
+// channels underflow.
+struct APRate {
+  double lam, l_ag, via_p, frac;
+};
+
+NB_HD __forceinline__ APRate ap_rate(double e_ag, double e_ap, double e_pg, double e_pa) {
+  APRate a;
+  a.l_ag = exp_tang(e_ag);
+  a.frac = 1.0 / (1.0 + exp_tang(e_pa - e_pg));
+  a.via_p = exp_tang(e_ap) * a.frac;
+  a.lam = a.l_ag + a.via_p;
+  return a;
+}
+
+// d ln lambda / dT9 from the channels' g = d ln lambda_c / dT9, with
+// d frac / dT9 = frac (1 - frac) (g_pg - g_pa)
+NB_HD __forceinline__ double ap_dlog(const APRate& a, double g_ag, double g_ap, double g_pg,
+                                     double g_pa) {
+  if (!finite_nonzero(a.lam)) return g_ag;
+  return (a.l_ag * g_ag + a.via_p * (g_ap + (1.0 - a.frac) * (g_pg - g_pa))) / a.lam;
+}
+
 // Rates near a reference temperature.  Within one step attempt T9 moves
 // only slightly from the predictor's value T9ref, where every k_r was
 // evaluated in full.  Then k_r(T9) = k_r(T9ref) exp(de_r) with

@@ -274,6 +274,23 @@ int build_blob(const nb_topology* T, const double* coeffs,
   }
 
   std::vector<double> coef(coeffs, coeffs + 7 * (size_t)R);
+  // effective (alpha,p)(p,gamma) rates: their three extra fits, one row each
+  std::vector<int32_t> ap(R, -1);
+  std::vector<double> apc;
+  if (T->ap_pg) {
+    if (!T->ap_coeffs) return NB_E_ARG;
+    for (int r = 0; r < R; ++r) {
+      if (T->ap_pg[r] == 0) continue;
+      if (T->ap_pg[r] != 1) return NB_E_ARG;
+      const double* b = T->ap_coeffs + 21 * (size_t)r;
+      for (int j = 0; j < 21; ++j)
+        if (!std::isfinite(b[j])) return NB_E_ARG;
+      ap[r] = (int32_t)(apc.size() / 21);
+      apc.insert(apc.end(), b, b + 21);
+    }
+  }
+  const int n_ap = (int)(apc.size() / 21);
+  if (apc.empty()) apc.push_back(0.0);
   std::vector<double> Q(R, 0.0), scale(R, 1.0);
   for (int r = 0; r < R; ++r) {
     if (T->Q) Q[r] = T->Q[r];
@@ -287,6 +304,9 @@ int build_blob(const nb_topology* T, const double* coeffs,
   h.n = n; h.N = N; h.R = R; h.self_heating = sh; h.has_E = hasE;
   h.nnz = nnz; h.nd = nd; h.nnz_jac = nnz_jac;
   h.o_coef = B.add(coef);
+  h.o_ap = B.add(ap);
+  h.o_apc = B.add(apc);
+  h.n_ap = n_ap;
   h.o_Q = B.add(Q);
   h.o_scale = B.add(scale);
   h.o_nrho = B.add(nrho);
@@ -351,8 +371,10 @@ int build_blob(const nb_topology* T, const double* coeffs,
     int64_t nl = piv[k].lend - piv[k].lbeg, nu = piv[k].uend - piv[k].ubeg;
     lu += nl + 2 * nl * nu;
   }
-  h.fl_teval = 2 + 14 * (int64_t)R;          // powers of T9, 7-term exponents, k_r
-  h.fl_teval_g = 6 + 10 * (int64_t)R;        // extra for d ln lambda / dT9
+  // powers of T9, 7-term exponents, k_r; an effective rate adds three
+  // exponents and their combination
+  h.fl_teval = 2 + 14 * (int64_t)R + 45 * (int64_t)n_ap;
+  h.fl_teval_g = 6 + 10 * (int64_t)R + 38 * (int64_t)n_ap;  // d ln lambda / dT9
   h.fl_terms = terms;                        // R_r = k_r prod Y
   h.fl_rhs = 2 * (int64_t)rhs_r.size() + (sh ? 2 * (int64_t)R + N + 5 : 0);
   h.fl_jac = jac;
@@ -360,7 +382,7 @@ int build_blob(const nb_topology* T, const double* coeffs,
   h.fl_solve = 2 * (int64_t)(fw_s.size() + bw_s.size()) + n;
   h.fl_edot = 2 * (int64_t)R;
   h.fl_tsolve = 2 * (int64_t)(tfw_s.size() + tbw_s.size()) + n;
-  h.n_exp_per_teval = R;
+  h.n_exp_per_teval = R + 2 * n_ap;
 
   std::memcpy(B.buf.data(), &h, sizeof(h));
   *out = std::move(B.buf);

@@ -67,3 +67,27 @@ def test_specialized_kernel_compiles_for_sm103a():
     assert "nb_spec_burn" in log and "sm_103a" in log
     m = re.search(r"Used (\d+) registers", log)
     assert m and int(m.group(1)) <= 255
+
+
+def test_effective_rates_in_the_source_and_checked_on_load():
+    # every (alpha,p)(p,gamma) rate combines its four channels through the
+    # shared helper, in the full evaluation and as the near evaluation's only
+    # path
+    net = gen.network("chain13_heat_ap")
+    n_ap = int(net.ap_pg.sum())
+    src = nb.specialized_source(net, 0)
+    assert src.count("const APRate q = ap_rate(e, eap, epg, epa);") == 2 * n_ap
+    assert src.count("w.g[") >= n_ap and "ap_dlog(q," in src
+    # a flag other than 0/1, a non-finite channel fit: rejected on the host
+    lib = _abi.load()
+    n = C.c_int64()
+    for bad in ("flag", "fit"):
+        spec = gen.network("chain13_heat_ap")
+        if bad == "flag":
+            spec.ap_pg = spec.ap_pg.copy()
+            spec.ap_pg[3] = 2
+        else:
+            spec.ap_coeffs = spec.ap_coeffs.copy()
+            spec.ap_coeffs[4, 1, 2] = float("nan")
+        arrays, topo, coef = nb._topology(spec)
+        assert lib.nb_specialize_source(C.byref(topo), coef, 0, None, 0, C.byref(n)) == -1

@@ -48,6 +48,7 @@ def gpu_run(nb, torch, net_c, z, s, **kw):
 
 
 CASES = [("chain13", 4096), ("chain13_literal", 1024), ("chain13_heat", 2048),
+         ("chain13_heat_ap", 2048),
          ("net48", 256), ("net48_adjoint", 128), ("net128_heat", 16)]
 
 

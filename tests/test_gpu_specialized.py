@@ -28,7 +28,8 @@ def _equal(a, b):
         assert torch.equal(x, y)
 
 
-CASES = [("chain13", 2048), ("chain13_literal", 1024), ("chain13_heat", 2048)]
+CASES = [("chain13", 2048), ("chain13_literal", 1024), ("chain13_heat", 2048),
+         ("chain13_heat_ap", 1024)]
 
 
 @pytest.mark.parametrize("variant", [1, 2, 3])

@@ -75,6 +75,94 @@ def test_rate_temperature_derivative_fd():
         np.testing.assert_allclose(g, fd, rtol=1e-6, atol=1e-8 * np.abs(g).max())
 
 
+# ------------------------------------------ effective (alpha,p)(p,gamma) rate
+
+def _ap_net(lams, reac=((0, 1),), prod=((2,),), N=3, scale=None):
+    """One A + alpha -> B reaction as the effective rate, with constant fits
+    lams = (ag, ap, pg, pa)."""
+    net = make_net(list(reac), list(prod), N=N, lam=[lams[0]], scale=scale)
+    net.ap_pg = np.ones(1, dtype=np.int8)
+    net.ap_coeffs = np.zeros((1, 3, 7))
+    net.ap_coeffs[0, :, 0] = np.log(np.asarray(lams[1:], dtype=np.float64))
+    return net
+
+
+def test_effective_rate_closed_form():
+    # lambda = ag + ap pg / (pg + pa) = 2 + 3 * 5 / 12, times s e^p rho^(n-1);
+    # constant fits have a zero temperature derivative
+    net = _ap_net((2.0, 3.0, 5.0, 7.0), scale=[0.5])
+    k, g = oracle.rate_factors(net, 1.7, 4.0, np.array([0.3]))
+    np.testing.assert_allclose(k, [0.5 * math.exp(0.3) * 4.0 * (2.0 + 3.0 * 5.0 / 12.0)],
+                               rtol=1e-15)
+    assert abs(g[0]) < 1e-15
+
+
+def test_effective_rate_limits():
+    # fast (p,g) against a vanishing (p,a): every (a,p) flow reaches B;
+    # vanishing (p,g): only the direct channel is left
+    k, _ = oracle.rate_factors(_ap_net((2.0, 3.0, 5.0, 1e-300)), 1.0, 1.0)
+    np.testing.assert_allclose(k, [5.0], rtol=1e-15)
+    k, _ = oracle.rate_factors(_ap_net((2.0, 3.0, 1e-300, 5.0)), 1.0, 1.0)
+    np.testing.assert_allclose(k, [2.0], rtol=1e-15)
+
+
+def test_effective_rate_from_the_fits_in_mpmath():
+    # each of the four channels evaluated from its fit in 50-digit arithmetic,
+    # then combined: the oracle's lambda and d ln lambda / dT9 (the latter by
+    # a central difference of the high-precision lambda)
+    net = gen.network("chain13_heat_ap")
+    mpmath.mp.dps = 50
+
+    def fit(a, T):
+        T = mpmath.mpf(T)
+        return mpmath.exp(a[0] + a[1] / T + a[2] * T ** (-mpmath.mpf(1) / 3)
+                          + a[3] * T ** (mpmath.mpf(1) / 3) + a[4] * T
+                          + a[5] * T ** (mpmath.mpf(5) / 3) + a[6] * mpmath.log(T))
+
+    def lam(r, T):
+        ag = fit([mpmath.mpf(float(v)) for v in net.coeffs[r]], T)
+        ap, pg, pa = (fit([mpmath.mpf(float(v)) for v in net.ap_coeffs[r, c]], T)
+                      for c in range(3))
+        return ag + ap * pg / (pg + pa)
+
+    for T9 in (0.6, 1.0, 2.9, 4.7):
+        k, g = oracle.rate_factors(net, T9, 1.0)
+        for r in np.nonzero(net.ap_pg)[0]:
+            assert abs(k[r] / float(lam(r, T9)) - 1) < 1e-13
+            h = mpmath.mpf("1e-20")
+            d = (mpmath.log(lam(r, T9 + h)) - mpmath.log(lam(r, T9 - h))) / (2 * h)
+            assert abs(g[r] - float(d)) <= 1e-12 * max(1.0, abs(float(d)))
+
+
+def test_effective_rate_equals_the_network_it_replaces():
+    # The approximation it stands for: A + a -> X + p, X + p -> A + a,
+    # X + p -> B and A + a -> B with proton capture on X fast, against the
+    # single effective A + a -> B.  With X and p made and destroyed in pairs,
+    # Y_X = Y_p = y relaxes to y^2 = ap Y_A Y_a / (pa + pg) within
+    # 1/(2 (pa + pg) y) ~ 2e-6 s, and holds y ~ 2e-7 of the flow; the burns
+    # agree to that order, while a wrong split of the flow (or a missing
+    # direct channel) changes Y_B by tens of percent.
+    ag, ap, pg, pa = 1.0, 10.0, 1e12, 3e11
+    full = make_net([(0, 1), (2, 3), (2, 3), (0, 1)], [(2, 3), (0, 1), (4,), (4,)],
+                    N=5, lam=[ap, pa, pg, ag], A=np.array([4.0, 12.0, 15.0, 1.0, 16.0]))
+    eff = _ap_net((ag, ap, pg, pa))
+    Y0f = np.array([0.2, 0.03, 0.0, 0.0, 0.0])
+    Y0e = np.array([0.2, 0.03, 0.0])
+    t_end = 0.1
+    of = oracle.burn(full, Y0f[None], np.array([1.0]), np.array([1.0]), t_end, 1e-10, 1e-20)
+    oe = oracle.burn(eff, Y0e[None], np.array([1.0]), np.array([1.0]), t_end, 1e-10, 1e-20)
+    assert of["status"][0] == 0 and oe["status"][0] == 0
+    yf, ye = of["Y"][0], oe["Y"][0]
+    assert 1e-8 < yf[2] < 1e-6 and abs(yf[2] - yf[3]) < 1e-12   # Y_X = Y_p, small
+    np.testing.assert_allclose([yf[0], yf[1], yf[4]], ye, rtol=1e-3)
+    # the closed form of the effective burn: A + a -> B at the constant rate
+    # L = ag + ap pg/(pg+pa), Y_a - Y_A = const: dY_A/dt = -L Y_A (Y_A + d)
+    L = ag + ap * pg / (pg + pa)
+    d = 0.2 - 0.03
+    YA = d * 0.03 / ((0.03 + d) * math.exp(L * d * t_end) - 0.03)
+    np.testing.assert_allclose(ye[1], YA, rtol=1e-8)
+
+
 # ---------------------------------------------------------------- RHS
 
 def test_rhs_single_reactions_by_hand():
