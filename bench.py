@@ -44,10 +44,17 @@ def dist_env():
     return ws, rank, local
 
 
+# the sources that determine the timed kernel's code: the integrator, the
+# exp, the compiled-network layout, the generic network walk and the code
+# generator of the specialised kernel, and the launch code
+KERNEL_SOURCES = ("integrator.cuh", "expf64.cuh", "blob.h", "device.cuh", "netload.cpp",
+                  "codegen.cpp", "burn.cu")
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2312_02836_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in KERNEL_SOURCES:
         with open(os.path.join(d, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -16,6 +16,7 @@
 // derivative through g_r = d ln lambda_r / dT9 when T9 is a parameter).
 // One lane per zone, K cotangent sets share each LU factorisation.
 #include <cuda_runtime.h>
+#include <cub/device/device_radix_sort.cuh>
 
 #include <algorithm>
 #include <cstring>
@@ -43,6 +44,7 @@ struct AdjParams {
   long long lane_doubles;  // adjoint workspace per lane
   int o_lam, o_ee, o_gr, o_gt, o_mu, o_de;
   unsigned long long* queue;
+  const int32_t* order;    // claim order (zone per claim), longest first, or null
 };
 
 struct AdjZone {
@@ -223,7 +225,7 @@ __global__ void __launch_bounds__(128) k_adjoint(AdjParams A) {
       if (!active && !retired) {
         const unsigned long long z = base + __popc(need & ((1u << lane) - 1u));
         if (z < (unsigned long long)A.Z) {
-          Zs.z = (long long)z;
+          Zs.z = A.order ? (long long)A.order[z] : (long long)z;
           active = true;
           fresh = true;
         } else {
@@ -246,6 +248,11 @@ __global__ void __launch_bounds__(128) k_adjoint(AdjParams A) {
       }
     }
   }
+}
+
+__global__ void k_zone_index(int32_t* idx, long long Z) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < Z) idx[i] = (int32_t)i;
 }
 
 }  // namespace
@@ -300,6 +307,28 @@ extern "C" int nb_burn_adjoint(nb_net net, void* tape, int32_t K, const double* 
   A.ws = net->ws_adj;
   A.queue = net->queue + 1;   // a second counter in the same allocation
   A.blob_in_smem = in_smem;
+  // Claim order: the tape holds every zone's step count, the exact length of
+  // its reverse sweep, so zones are claimed longest first and the last lanes
+  // to finish run short zones (one lane per zone otherwise waits on the
+  // longest zone).
+  if (Z > 1 && Z <= 0x7fffffffLL) {
+    size_t temp = 0;
+    CK(cub::DeviceRadixSort::SortPairsDescending(nullptr, temp, (const int32_t*)nullptr,
+                                                 (int32_t*)nullptr, (const int32_t*)nullptr,
+                                                 (int32_t*)nullptr, (int)Z, 0, 32, st));
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t ib = al((size_t)Z * 4);
+    rc = nb::ensure((void**)&net->sched_adj, &net->sched_adj_bytes, 3 * ib + al(temp));
+    if (rc) return rc;
+    int32_t* k_out = (int32_t*)net->sched_adj;
+    int32_t* i_in = (int32_t*)(net->sched_adj + ib);
+    int32_t* i_out = (int32_t*)(net->sched_adj + 2 * ib);
+    k_zone_index<<<(unsigned)((Z + 255) / 256), 256, 0, st>>>(i_in, Z);
+    CK(cudaGetLastError());
+    CK(cub::DeviceRadixSort::SortPairsDescending(net->sched_adj + 3 * ib, temp, tp->dev.steps,
+                                                 k_out, i_in, i_out, (int)Z, 0, 32, st));
+    A.order = i_out;
+  }
   CK(cudaMemsetAsync(A.queue, 0, sizeof(unsigned long long), st));
   k_adjoint<<<(unsigned)blocks, tpb, dyn, st>>>(A);
   CK(cudaGetLastError());

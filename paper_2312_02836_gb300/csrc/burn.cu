@@ -191,6 +191,7 @@ int nb_net_free(nb_net net) {
   if (net->stage) cudaFree(net->stage);
   if (net->ws_adj) cudaFree(net->ws_adj);
   if (net->sched) cudaFree(net->sched);
+  if (net->sched_adj) cudaFree(net->sched_adj);
   for (auto& sp : net->spec)
     if (sp.lib) cudaLibraryUnload(sp.lib);
   delete net;

@@ -27,6 +27,8 @@ struct nb_net_s {
   size_t ws_adj_bytes = 0;
   unsigned char* sched = nullptr;   // claim-order keys, indices, sort scratch
   size_t sched_bytes = 0;
+  unsigned char* sched_adj = nullptr;   // the adjoint's claim order and sort scratch
+  size_t sched_adj_bytes = 0;
   // network-specialised kernels by storage variant (1..3): 0 not built,
   // 1 loaded, -1 failed (log kept)
   struct Spec {
