@@ -61,10 +61,13 @@ def kernel_source_hash() -> str:
 
 
 def launch_shape(launch, variant):
-    """tpb,bps,ws_in_shared,specialised variant of a persistent launch."""
-    return "%d,%d,%d,%d" % (launch.get("threads_per_block", 0) or 128,
-                            launch.get("blocks_per_sm", 0) or 1,
-                            max(launch.get("ws_in_shared", 0), 0), variant)
+    """lanes per SM and specialised variant of a persistent launch (what sets
+    the lanes in flight and the code of the kernel); None with shared-memory
+    work arrays, which the profile does not cover."""
+    if launch.get("ws_in_shared", -1) > 0:
+        return None
+    return "%d,%d" % ((launch.get("threads_per_block", 0) or 128) *
+                      (launch.get("blocks_per_sm", 0) or 1), variant)
 
 
 def profiled_traffic(kernel, Z, shape):
