@@ -146,7 +146,7 @@ def sampled_parity(name, net, z, s, out, n) -> dict:
     Z = z["T9"].shape[0]
     sel = np.unique(np.random.default_rng(12345).choice(Z, min(n, Z), replace=False))
     o = oracle.burn(net, z["Y"][sel], z["T9"][sel], z["rho"][sel], s["t_end"], s["rtol"],
-                    s["atol"])
+                    s["atol"], zeta=z["zeta"][sel] if "zeta" in z else None)
     g = {k: v[sel] for k, v in to_numpy(out).items()}
     keep = np.ones(sel.size, dtype=bool)
     if name == "net128_heat":
@@ -171,7 +171,8 @@ def cpu_baseline(name: str, Z_sample: int, zone_offset: int = 0) -> dict:
     net, z, s = gen.problem(name, zone_offset + Z_sample)
     z = {k: v[zone_offset:] for k, v in z.items()}
     t0 = time.perf_counter()
-    out = oracle.burn(net, z["Y"], z["T9"], z["rho"], s["t_end"], s["rtol"], s["atol"])
+    out = oracle.burn(net, z["Y"], z["T9"], z["rho"], s["t_end"], s["rtol"], s["atol"],
+                      zeta=z.get("zeta"))
     dt = time.perf_counter() - t0
     return {"value": Z_sample / dt, "unit": "zone-burns/s", "cores": int(out["threads"]),
             "kind": "oracle", "seconds": dt,
@@ -231,6 +232,8 @@ def run_native(args):
     Y0 = torch.from_numpy(z["Y"]).to(dev)
     T9 = torch.from_numpy(z["T9"]).to(dev)
     rho = torch.from_numpy(z["rho"]).to(dev)
+    # a screened workload's per-zone plasma parameter, given to every burn
+    zk = dict(zeta=torch.from_numpy(z["zeta"]).to(dev)) if "zeta" in z else {}
     out = None
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -251,14 +254,14 @@ def run_native(args):
         tune_ms = None
     else:
         from paper_2312_02836_gb300.autotune import autotune
-        launch = autotune(netc, Y0, T9, rho, s["t_end"], s["rtol"], s["atol"])
+        launch = autotune(netc, Y0, T9, rho, s["t_end"], s["rtol"], s["atol"], extra=zk)
         tune_ms = launch.pop("_timings_ms")
 
     def step(kernel="persistent"):
         nonlocal out
         opts = launch if kernel == "persistent" else {}
         out = nb.burn(netc, Y0, T9, rho, s["t_end"], s["rtol"], s["atol"],
-                      kernel=kernel, out=out, **opts)
+                      kernel=kernel, out=out, **opts, **zk)
 
     for _ in range(args.warmup):
         step()
@@ -296,14 +299,15 @@ def run_native(args):
                 counters=torch.empty((Z, 8), dtype=torch.int32).pin_memory().numpy(),
                 status=torch.empty(Z, dtype=torch.int32).pin_memory().numpy())
     if not args.no_e2e:
-        nb.burn_host(netc, hY0, hT9, hrho, s["t_end"], s["rtol"], s["atol"], out=hout, **launch)
+        nb.burn_host(netc, hY0, hT9, hrho, s["t_end"], s["rtol"], s["atol"], out=hout,
+                     **launch, **zk)
     e2e_t = []
     for _ in range(0 if args.no_e2e else max(2, min(args.steps, 5))):
         flush.fill_(1.0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         nb.burn_host(netc, hY0, hT9, hrho, s["t_end"], s["rtol"], s["atol"], out=hout,
-                     **launch)
+                     **launch, **zk)
         e2e_t.append(time.perf_counter() - t0)
     if e2e_t:
         assert np.array_equal(hout["Y"], out.Y.cpu().numpy())

@@ -56,6 +56,14 @@ CONFIGS = {
                             T9=(0.5, 5.0), rho=(1e5, 1e8), t_end=1e-3,
                             rtol=1e-8, atol=1e-12, zone_seed=1001, Q=True,
                             ap_from=1),
+    # The self-heating chain with weak screening of every rate: charges
+    # Z_i = A_i / 2, and a synthetic plasma parameter per zone, zeta ~ U[1, 2]
+    # (the chain's initial composition gives 1.5).  Same zones as
+    # chain13_heat otherwise.
+    "chain13_heat_scr": dict(kind="chain", literal=False, heat=True, Z=65536,
+                             T9=(0.5, 5.0), rho=(1e5, 1e8), t_end=1e-3,
+                             rtol=1e-8, atol=1e-12, zone_seed=1001, Q=True,
+                             screen=True, zeta=(1.0, 2.0)),
     # Random sparse network, 48 species / 180 rates, fixed T and rho.
     "net48": dict(kind="random", N=48, mix=(60, 100, 20), topo_seed=2,
                   heat=False, Z=262144, T9=(0.3, 6.0), rho=(1e4, 1e9),
@@ -93,6 +101,9 @@ class NetworkSpec:
     # ap_coeffs [R, 3, 7] fits of the (a,p), (p,g) and (p,a) channels
     ap_pg: Optional[np.ndarray] = None
     ap_coeffs: Optional[np.ndarray] = None
+    # weak-screening strength per reaction, s_r = 0.188 sum Z_a Z_b over the
+    # reactants' successive pairs, or None
+    screen: Optional[np.ndarray] = None
     extra: dict = field(default_factory=dict)
 
 
@@ -107,6 +118,21 @@ def _draw_coeffs(rng: np.random.Generator, R: int) -> np.ndarray:
     c[:, 3:6] = a345.T
     c[:, 6] = a6
     return c
+
+
+def _screen_strengths(reac: np.ndarray, charge: np.ndarray) -> np.ndarray:
+    """s_r = 0.188 (Z_1 Z_2 + (Z_1 + Z_2) Z_3 + ...): the weak-screening
+    coefficient of each reaction, the reactants taken as successive pairs
+    (a capture on the compound of the ones before).  One-body: 0."""
+    out = np.zeros(reac.shape[0])
+    for r in range(reac.shape[0]):
+        zs = [charge[int(v)] for v in reac[r] if v >= 0]
+        acc, zsum = 0.0, zs[0]
+        for zb in zs[1:]:
+            acc += zsum * zb
+            zsum += zb
+        out[r] = 0.188 * acc
+    return out
 
 
 def _pad3(t):
@@ -223,10 +249,13 @@ def network(name: str) -> NetworkSpec:
                 f = _draw_coeffs(rng, R)
                 f[:, 0] += shift            # proton capture faster than (a,p)
                 ap_coeffs[:, c, :] = f
+        screen = None
+        if cfg.get("screen"):
+            screen = _screen_strengths(reac, ALPHA_CHAIN_A / 2.0)
         return NetworkSpec(name=name, N=13, R=R, reactants=reac, products=prod,
                            A=ALPHA_CHAIN_A.copy(), coeffs=coeffs, Q=Q,
                            self_heating=cfg["heat"], seed_used=0,
-                           ap_pg=ap_pg, ap_coeffs=ap_coeffs)
+                           ap_pg=ap_pg, ap_coeffs=ap_coeffs, screen=screen)
     N = cfg["N"]
     seed = cfg["topo_seed"]
     while True:
@@ -267,8 +296,15 @@ def zones(name: str, Z: Optional[int] = None) -> dict:
         X = X / X.sum(axis=1, keepdims=True)
         Y = np.zeros((Z, N), dtype=np.float64)
         Y[:, :4] = X / np.arange(1, 5, dtype=np.float64)[None, :]
-    return dict(T9=np.ascontiguousarray(T9), rho=np.ascontiguousarray(rho),
-                Y=np.ascontiguousarray(Y))
+    out = dict(T9=np.ascontiguousarray(T9), rho=np.ascontiguousarray(rho),
+               Y=np.ascontiguousarray(Y))
+    if cfg.get("zeta") is not None:
+        # a fourth child stream: the first three stay those of the other keys
+        s_z = np.random.SeedSequence(cfg["zone_seed"]).spawn(4)[3]
+        lo, hi = cfg["zeta"]
+        out["zeta"] = np.ascontiguousarray(
+            np.random.Generator(np.random.PCG64(s_z)).uniform(lo, hi, Z))
+    return out
 
 
 def problem(name: str, Z: Optional[int] = None):

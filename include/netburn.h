@@ -100,6 +100,12 @@ typedef struct {
    * and the multiplier p_r scales the whole effective rate. */
   const int8_t* ap_pg;
   const double* ap_coeffs;
+  /* Weak screening (Salpeter 1954): R_r is multiplied by exp(H_r),
+   * H_r = s_r sqrt(rho zeta) T6^(-3/2), T6 = 1e3 T9.  screen [R] or NULL (no
+   * screening): s_r = 0.188 sum Z_a Z_b over the reactants' successive
+   * pairs.  zeta, the plasma parameter sum (Z_i^2 + Z_i) Y_i, is a per-zone
+   * input (nb_options.zeta_zone) held over the burn. */
+  const double* screen;
 } nb_topology;
 
 typedef struct {
@@ -172,6 +178,11 @@ typedef struct {
                                ends every zone it claims after that the same
                                way, so the call always finishes.  0: none.
                                Ignored by nb_burn_batch_noalloc. */
+  const double* zeta_zone;  /* [Z] device array of per-zone plasma parameters
+                               for screening, or NULL (no screening).  A
+                               negative or non-finite entry gives that zone
+                               NB_Z_NONFINITE.  Ignored by
+                               nb_burn_batch_noalloc. */
 } nb_options;
 
 #define NB_KERNEL_PERSISTENT 0  /* lane-per-zone, device work queue */
@@ -287,6 +298,7 @@ typedef struct {
   const double* ln_mult;    /* NULL, [R] or [Z, R] */
   int32_t ln_mult_per_zone;
   const double* t_end_zone; /* [Z] or NULL */
+  const double* zeta_zone;  /* [Z] plasma parameters (screening) or NULL */
   double* Y;                /* [Z, N] out */
   double* T9;               /* [Z] out */
   double* E;                /* [Z] out or NULL */

@@ -51,7 +51,8 @@ class _Net(C.Structure):
     _fields_ = [("N", C.c_int32), ("R", C.c_int32), ("self_heating", C.c_int32),
                 ("reactants", C.c_void_p), ("products", C.c_void_p),
                 ("Q", C.c_void_p), ("scale", C.c_void_p), ("coeffs", C.c_void_p),
-                ("ap_pg", C.c_void_p), ("ap_coeffs", C.c_void_p)]
+                ("ap_pg", C.c_void_p), ("ap_coeffs", C.c_void_p),
+                ("screen", C.c_void_p)]
 
 
 class _Opt(C.Structure):
@@ -67,20 +68,20 @@ def _load():
         if _lib is None:
             lib = C.CDLL(build())
             P, I32, I64, D = C.c_void_p, C.c_int32, C.c_int64, C.c_double
-            lib.ora_rate_factors.argtypes = [P, D, D, P, P, P]
-            lib.ora_rhs.argtypes = [P, P, D, D, P, P, P]
-            lib.ora_jacobian.argtypes = [P, P, D, D, P, P]
+            lib.ora_rate_factors.argtypes = [P, D, D, D, P, P, P]
+            lib.ora_rhs.argtypes = [P, P, D, D, D, P, P, P]
+            lib.ora_jacobian.argtypes = [P, P, D, D, D, P, P]
             lib.ora_bdf_alpha.argtypes = [I32, D, P, D, P]
             lib.ora_extrapolate.argtypes = [I32, I32, P, P, D, P]
             lib.ora_burn_batch.argtypes = [P, P, I64, P, P, P, P, I32, P, P, P,
-                                           P, P, I32, P]
+                                           P, P, I32, P, P]
             lib.ora_burn_batch.restype = I32
-            lib.ora_burn_tape.argtypes = [P, P, P, D, D, P, P, P, P, P, I32, P,
+            lib.ora_burn_tape.argtypes = [P, P, P, D, D, D, P, P, P, P, P, I32, P,
                                           P, P, P, P]
             lib.ora_burn_tape.restype = I32
-            lib.ora_replay.argtypes = [P, P, P, D, D, P, I32, P, P, D, I32, P, P]
+            lib.ora_replay.argtypes = [P, P, P, D, D, D, P, I32, P, P, D, I32, P, P]
             lib.ora_replay.restype = I32
-            lib.ora_forward_sensitivity.argtypes = [P, D, D, P, I32, P, P, P, P, P]
+            lib.ora_forward_sensitivity.argtypes = [P, D, D, D, P, I32, P, P, P, P, P]
             lib.ora_forward_sensitivity.restype = I32
             _lib = lib
     return _lib
@@ -110,6 +111,7 @@ class Network:
         ap = getattr(spec, "ap_pg", None)
         self.ap_pg = None if ap is None else np.ascontiguousarray(ap, dtype=np.int8)
         self.ap_coeffs = _f64(getattr(spec, "ap_coeffs", None))
+        self.screen = _f64(getattr(spec, "screen", None))
         if self.ap_pg is not None and (self.ap_coeffs is None
                                        or self.ap_coeffs.size != 21 * self.R):
             raise ValueError("ap_pg needs ap_coeffs [R, 3, 7]")
@@ -119,7 +121,7 @@ class Network:
         self._s = _Net(self.N, self.R, int(self.self_heating),
                        _p(self.reactants), _p(self.products), _p(self.Q),
                        _p(self.scale), _p(self.coeffs), _p(self.ap_pg),
-                       _p(self.ap_coeffs))
+                       _p(self.ap_coeffs), _p(self.screen))
 
     @property
     def ptr(self):
@@ -136,18 +138,19 @@ def _opts(t_end, rtol, atol, max_attempts=500000, newton_tol=1e-3,
                 fixed_h, fixed_order, max_order)
 
 
-def rate_factors(net, T9, rho, ln_mult=None):
-    """k_r = s_r e^p_r rho^(n_r-1) lambda_r(T9) and d ln lambda_r / dT9."""
+def rate_factors(net, T9, rho, ln_mult=None, zeta=0.0):
+    """k_r = s_r e^p_r rho^(n_r-1) lambda_r(T9) exp(H_r) and d ln k_r / dT9
+    (H_r the weak-screening exponent at plasma parameter zeta)."""
     net = _net(net)
     lib = _load()
     k = np.empty(net.R)
     g = np.empty(net.R)
     lm = _f64(ln_mult)
-    lib.ora_rate_factors(net.ptr, float(T9), float(rho), _p(lm), _p(k), _p(g))
+    lib.ora_rate_factors(net.ptr, float(T9), float(rho), float(zeta), _p(lm), _p(k), _p(g))
     return k, g
 
 
-def rhs(net, x, T9=0.0, rho=1.0, ln_mult=None):
+def rhs(net, x, T9=0.0, rho=1.0, ln_mult=None, zeta=0.0):
     """f(x) [n] and edot at state x (x[N] is T9 under self-heating)."""
     net = _net(net)
     lib = _load()
@@ -155,19 +158,19 @@ def rhs(net, x, T9=0.0, rho=1.0, ln_mult=None):
     f = np.empty(net.n)
     ed = C.c_double(0.0)
     lm = _f64(ln_mult)
-    lib.ora_rhs(net.ptr, _p(x), float(T9), float(rho), _p(lm), _p(f),
+    lib.ora_rhs(net.ptr, _p(x), float(T9), float(rho), float(zeta), _p(lm), _p(f),
                 C.byref(ed))
     return f, ed.value
 
 
-def jacobian(net, x, T9=0.0, rho=1.0, ln_mult=None):
+def jacobian(net, x, T9=0.0, rho=1.0, ln_mult=None, zeta=0.0):
     """Analytic Jacobian df/dx [n, n]."""
     net = _net(net)
     lib = _load()
     x = _f64(x)
     J = np.empty((net.n, net.n))
     lm = _f64(ln_mult)
-    lib.ora_jacobian(net.ptr, _p(x), float(T9), float(rho), _p(lm), _p(J))
+    lib.ora_jacobian(net.ptr, _p(x), float(T9), float(rho), float(zeta), _p(lm), _p(J))
     return J
 
 
@@ -192,8 +195,10 @@ def extrapolate(t_pts, x_pts, t):
     return out
 
 
-def burn(net, Y0, T9, rho, t_end, rtol, atol, ln_mult=None, threads=0, **opts):
-    """Burn Z zones.  t_end is a number or a per-zone array [Z].  Returns
+def burn(net, Y0, T9, rho, t_end, rtol, atol, ln_mult=None, threads=0, zeta=None,
+         **opts):
+    """Burn Z zones.  t_end is a number or a per-zone array [Z]; zeta None or
+    the per-zone plasma parameters [Z] for screening.  Returns
     dict(Y, T9, E, counters [Z, 8], status, threads)."""
     net = _net(net)
     lib = _load()
@@ -215,15 +220,16 @@ def burn(net, Y0, T9, rho, t_end, rtol, atol, ln_mult=None, threads=0, **opts):
     if np.ndim(t_end) > 0:
         tz = _f64(t_end)
         t_end = 0.0
+    zt = None if zeta is None else _f64(np.broadcast_to(np.asarray(zeta, dtype=np.float64), (Z,)))
     o = _opts(float(t_end), rtol, atol, **opts)
     used = lib.ora_burn_batch(net.ptr, C.addressof(o), Z, _p(Y0), _p(T9),
                               _p(rho), _p(lm), per_zone, _p(Y), _p(T9o), _p(E),
-                              _p(cnt), _p(st), int(threads), _p(tz))
+                              _p(cnt), _p(st), int(threads), _p(tz), _p(zt))
     return dict(Y=Y, T9=T9o, E=E, counters=cnt, status=st, threads=used)
 
 
 def burn_tape(net, Y0, T9, rho, t_end, rtol, atol, ln_mult=None, cap=200000,
-              **opts):
+              zeta=0.0, **opts):
     """One zone with its accepted schedule: dict(Y, T9, E, counters, status,
     t [S+1], k [S+1], x [S+1, n], Ehist [S+1])."""
     net = _net(net)
@@ -241,7 +247,7 @@ def burn_tape(net, Y0, T9, rho, t_end, rtol, atol, ln_mult=None, cap=200000,
     count = C.c_int32(0)
     o = _opts(t_end, rtol, atol, **opts)
     st = lib.ora_burn_tape(net.ptr, C.addressof(o), _p(Y0), float(T9),
-                           float(rho), _p(lm), _p(Y), C.byref(T9o), C.byref(E),
+                           float(rho), float(zeta), _p(lm), _p(Y), C.byref(T9o), C.byref(E),
                            _p(cnt), cap, _p(tt), _p(tk), _p(tx), _p(tE),
                            C.byref(count))
     c = count.value
@@ -251,7 +257,7 @@ def burn_tape(net, Y0, T9, rho, t_end, rtol, atol, ln_mult=None, cap=200000,
 
 
 def replay(net, Y0, T9, rho, t, k, rtol, atol, ln_mult=None, tol=1e-6,
-           maxit=50):
+           maxit=50, zeta=0.0):
     """Final (x [n], E) of the frozen schedule (t, k), full Newton to tol
     (weighted norm) and one further iteration."""
     net = _net(net)
@@ -264,14 +270,14 @@ def replay(net, Y0, T9, rho, t, k, rtol, atol, ln_mult=None, tol=1e-6,
     E = C.c_double(0.0)
     o = _opts(float(t[-1]), rtol, atol)
     rc = lib.ora_replay(net.ptr, C.addressof(o), _p(Y0), float(T9), float(rho),
-                        _p(lm), int(t.shape[0] - 1), _p(t), _p(k), float(tol),
+                        float(zeta), _p(lm), int(t.shape[0] - 1), _p(t), _p(k), float(tol),
                         int(maxit), _p(x), C.byref(E))
     if rc != 0:
         raise RuntimeError("replay did not converge")
     return x, E.value
 
 
-def forward_sensitivity(net, T9, rho, t, k, x, ln_mult=None):
+def forward_sensitivity(net, T9, rho, t, k, x, ln_mult=None, zeta=0.0):
     """d x_final / d theta [n, P] and d E_final / d theta [P] along a recorded
     schedule; theta = (ln multipliers [R], x0 [n], T9 if not self-heating)."""
     net = _net(net)
@@ -283,7 +289,7 @@ def forward_sensitivity(net, T9, rho, t, k, x, ln_mult=None):
     P = net.R + net.n + (0 if net.self_heating else 1)
     dx = np.empty((net.n, P))
     dE = np.empty(P)
-    rc = lib.ora_forward_sensitivity(net.ptr, float(T9), float(rho), _p(lm),
+    rc = lib.ora_forward_sensitivity(net.ptr, float(T9), float(rho), float(zeta), _p(lm),
                                      int(t.shape[0] - 1), _p(t), _p(k), _p(x),
                                      _p(dx), _p(dE))
     if rc != 0:

@@ -18,6 +18,11 @@
  *   RHS         dY_i/dt = sum_r c_ir R_r,  c_ir = #(i in products) - #(i in reactants)
  *   energy      edot = sum_r Q_r R_r,  dE/dt = edot
  *   heating     dT9/dt = edot / c_v,  c_v = 1.5 sum_i Y_i + 1e-3 T9^3
+ *   screening   weak screening (Salpeter 1954): R_r is multiplied by exp(H_r),
+ *               H_r = s_r sqrt(rho zeta) T6^(-3/2), T6 = 1e3 T9, where
+ *               s_r = 0.188 sum Z_a Z_b over the reactants' successive pairs
+ *               (given per reaction) and zeta the zone's plasma parameter
+ *               sum (Z_i^2 + Z_i) Y_i, an input of the zone held over its burn
  *   effective   a reaction flagged as the (alpha,p)(p,gamma) approximation of
  *               Sec. 2 (A(a,p)X(p,g)B merged into one A(a,g)B rate, valid
  *               when proton capture on X is fast, so that the proton flow
@@ -95,6 +100,7 @@ typedef struct {
     const double* coeffs;       /* [R*7] */
     const int8_t* ap_pg;        /* [R] or NULL: 1 = (alpha,p)(p,gamma) effective */
     const double* ap_coeffs;    /* [R*21] fits of (a,p), (p,g), (p,a), or NULL */
+    const double* screen;       /* [R] weak-screening strengths s_r, or NULL */
 } ora_network;
 
 typedef struct {
@@ -128,7 +134,7 @@ static double stoich(const ora_network* net, int i, int r) {
 }
 
 /* k_r = s_r e^(p_r) rho^(n_r-1) lambda_r(T9) and g_r = d ln lambda_r / dT9 */
-void ora_rate_factors(const ora_network* net, double T9, double rho,
+void ora_rate_factors(const ora_network* net, double T9, double rho, double zeta,
                       const double* ln_mult, double* k, double* g) {
     double t13 = cbrt(T9);
     double phi[7] = {1.0, 1.0 / T9, 1.0 / t13, t13, T9, T9 * t13 * t13, log(T9)};
@@ -150,6 +156,12 @@ void ora_rate_factors(const ora_network* net, double T9, double rho,
         double p = ln_mult ? ln_mult[r] : 0.0;
         double rp = 1.0;
         for (int m = 1; m < n_reactants(net, r); ++m) rp *= rho;
+        /* screening: H_r = s_r sqrt(rho zeta) T6^(-3/2), dH/dT9 = -1.5 H / T9 */
+        double H = 0.0;
+        if (net->screen && zeta > 0.0)
+            H = net->screen[r] * sqrt(rho * zeta) * pow(1e3 * T9, -1.5);
+        e += H;
+        de += -1.5 * H / T9;
         double lam = exp(e);
         if (net->ap_pg && net->ap_pg[r]) {
             /* lambda = lambda_ag + lambda_ap lambda_pg / (lambda_pg + lambda_pa) */
@@ -163,6 +175,9 @@ void ora_rate_factors(const ora_network* net, double T9, double rho,
                     dec[c] += b[j] * dphi[j];
                 }
             }
+            /* the alpha capture screens the (a,p) channel as it does the direct one */
+            ec[0] += H;
+            dec[0] += -1.5 * H / T9;
             double l_ag = lam, l_ap = exp(ec[0]), l_pg = exp(ec[1]), l_pa = exp(ec[2]);
             double frac = l_pg / (l_pg + l_pa);
             double via_p = l_ap * frac;
@@ -309,12 +324,12 @@ static int state_dim(const ora_network* net) { return net->N + (net->self_heatin
 
 /* Public single-state evaluations (used by the tests).  T9 is the fixed
    temperature when the network has no self-heating; otherwise x[N] is used. */
-void ora_rhs(const ora_network* net, const double* x, double T9, double rho,
+void ora_rhs(const ora_network* net, const double* x, double T9, double rho, double zeta,
              const double* ln_mult, double* f, double* edot) {
     double* k = malloc(sizeof(double) * (net->R + 1));
     double* Rr = malloc(sizeof(double) * (net->R + 1));
     rxn_species* L = species_lists(net);
-    ora_rate_factors(net, net->self_heating ? x[net->N] : T9, rho, ln_mult, k, NULL);
+    ora_rate_factors(net, net->self_heating ? x[net->N] : T9, rho, zeta, ln_mult, k, NULL);
     rhs_given_k(net, L, x, k, f, edot, Rr);
     free(L);
     free(k);
@@ -322,12 +337,12 @@ void ora_rhs(const ora_network* net, const double* x, double T9, double rho,
 }
 
 void ora_jacobian(const ora_network* net, const double* x, double T9, double rho,
-                  const double* ln_mult, double* J) {
+                  double zeta, const double* ln_mult, double* J) {
     double* k = malloc(sizeof(double) * (net->R + 1));
     double* g = malloc(sizeof(double) * (net->R + 1));
     double* Rr = malloc(sizeof(double) * (net->R + 1));
     rxn_species* L = species_lists(net);
-    ora_rate_factors(net, net->self_heating ? x[net->N] : T9, rho, ln_mult, k, g);
+    ora_rate_factors(net, net->self_heating ? x[net->N] : T9, rho, zeta, ln_mult, k, g);
     jacobian_given_k(net, L, x, k, g, J, Rr);
     free(L);
     free(k);
@@ -484,13 +499,14 @@ typedef struct {
     double rho, T9_fixed;
     const double* ln_mult;
     int32_t* cnt;
+    double zeta;
 } zone_ctx;
 
 /* rate factors for state x (fixed temperature or x[N]) */
 static void rates_for(zone_ctx* z, const double* x, work_t* W, int with_g) {
     const ora_network* net = z->net;
     double T9 = net->self_heating ? x[net->N] : z->T9_fixed;
-    ora_rate_factors(net, T9, z->rho, z->ln_mult, W->k, with_g ? W->g : NULL);
+    ora_rate_factors(net, T9, z->rho, z->zeta, z->ln_mult, W->k, with_g ? W->g : NULL);
     z->cnt[C_TEVAL]++;
 }
 
@@ -523,14 +539,14 @@ static double order_estimate(int q, int n, work_t* W, double h) {
 }
 
 static int burn_zone(const ora_network* net, const ora_options* opt,
-                     const double* Y0, double T9_0, double rho,
+                     const double* Y0, double T9_0, double rho, double zeta,
                      const double* ln_mult, double* Y_out, double* T9_out,
                      double* E_out, int32_t* cnt, ora_tape* tape, work_t* W) {
     const int N = net->N, n = state_dim(net);
     const int has_E = net->Q != NULL;
     const double t_end = opt->t_end, rtol = opt->rtol, atol = opt->atol;
     const int kmax = opt->max_order > 0 && opt->max_order < KMAX ? opt->max_order : KMAX;
-    zone_ctx z = {net, rho, T9_0, ln_mult, cnt};
+    zone_ctx z = {net, rho, T9_0, ln_mult, cnt, zeta};
     double* f0 = malloc(sizeof(double) * n);   /* f(x_0), for the first predictor */
     memset(cnt, 0, sizeof(int32_t) * C_COUNT);
 
@@ -729,7 +745,7 @@ typedef struct {
     const ora_options* opt;
     int64_t Z;
     const double* t_end_z;      /* per-zone end times or NULL */
-    const double *Y0, *T9, *rho, *ln_mult;
+    const double *Y0, *T9, *rho, *ln_mult, *zeta;
     int per_zone_mult;
     double *Y, *T9_out, *E;
     int32_t *cnt, *status;
@@ -757,7 +773,8 @@ static void* batch_worker(void* arg) {
             continue;
         }
         B->status[z] = burn_zone(net, &oz, B->Y0 + (size_t)z * net->N, B->T9[z],
-                                 B->rho[z], lm, B->Y + (size_t)z * net->N,
+                                 B->rho[z], B->zeta ? B->zeta[z] : 0.0, lm,
+                                 B->Y + (size_t)z * net->N,
                                  B->T9_out ? B->T9_out + z : NULL,
                                  B->E ? B->E + z : NULL,
                                  B->cnt + (size_t)z * C_COUNT, NULL, W);
@@ -769,13 +786,14 @@ static void* batch_worker(void* arg) {
 /* Burn Z zones.  Y0 [Z*N], T9 [Z], rho [Z]; ln_mult [R] shared or [Z*R];
    outputs Y [Z*N], T9_out [Z], E [Z] (may be NULL), cnt [Z*8], status [Z].
    nthreads <= 0 means one thread per online core.  t_end_z: per-zone end
-   times (each zone burns for its own step) or NULL for opt->t_end.
+   times (each zone burns for its own step) or NULL for opt->t_end.  zeta:
+   per-zone plasma parameters for screening, or NULL (no screening).
    Returns the threads used. */
 int ora_burn_batch(const ora_network* net, const ora_options* opt, int64_t Z,
                    const double* Y0, const double* T9, const double* rho,
                    const double* ln_mult, int per_zone_mult, double* Y,
                    double* T9_out, double* E, int32_t* cnt, int32_t* status,
-                   int nthreads, const double* t_end_z) {
+                   int nthreads, const double* t_end_z, const double* zeta) {
     if (nthreads <= 0) {
         long c = sysconf(_SC_NPROCESSORS_ONLN);
         nthreads = c > 0 ? (int)c : 1;
@@ -783,7 +801,7 @@ int ora_burn_batch(const ora_network* net, const ora_options* opt, int64_t Z,
     if (nthreads > Z) nthreads = Z > 0 ? (int)Z : 1;
     batch_t B;
     B.net = net; B.opt = opt; B.Z = Z; B.t_end_z = t_end_z; B.Y0 = Y0; B.T9 = T9; B.rho = rho;
-    B.ln_mult = ln_mult; B.per_zone_mult = per_zone_mult; B.Y = Y;
+    B.ln_mult = ln_mult; B.per_zone_mult = per_zone_mult; B.Y = Y; B.zeta = zeta;
     B.T9_out = T9_out; B.E = E; B.cnt = cnt; B.status = status;
     atomic_init(&B.next, 0);
     pthread_t* th = malloc(sizeof(pthread_t) * nthreads);
@@ -795,13 +813,13 @@ int ora_burn_batch(const ora_network* net, const ora_options* opt, int64_t Z,
 
 /* One zone with its accepted schedule recorded (t, k, x, E per point). */
 int ora_burn_tape(const ora_network* net, const ora_options* opt,
-                  const double* Y0, double T9_0, double rho, const double* ln_mult,
-                  double* Y, double* T9_out, double* E, int32_t* cnt,
-                  int32_t cap, double* tape_t, int32_t* tape_k, double* tape_x,
-                  double* tape_E, int32_t* tape_count) {
+                  const double* Y0, double T9_0, double rho, double zeta,
+                  const double* ln_mult, double* Y, double* T9_out, double* E,
+                  int32_t* cnt, int32_t cap, double* tape_t, int32_t* tape_k,
+                  double* tape_x, double* tape_E, int32_t* tape_count) {
     work_t* W = work_alloc(net);
     ora_tape tp = {cap, tape_t, tape_k, tape_x, tape_E, 0};
-    int st = burn_zone(net, opt, Y0, T9_0, rho, ln_mult, Y, T9_out, E, cnt, &tp, W);
+    int st = burn_zone(net, opt, Y0, T9_0, rho, zeta, ln_mult, Y, T9_out, E, cnt, &tp, W);
     *tape_count = tp.count;
     work_free(W);
     return st;
@@ -816,13 +834,13 @@ int ora_burn_tape(const ora_network* net, const ora_options* opt,
    iteration.  Output the
    final state x_S [n] and E_S.  Returns 0, or -1 if a step did not converge. */
 int ora_replay(const ora_network* net, const ora_options* opt, const double* Y0,
-               double T9_0, double rho, const double* ln_mult, int32_t S,
+               double T9_0, double rho, double zeta, const double* ln_mult, int32_t S,
                const double* tape_t, const int32_t* tape_k, double tol,
                int32_t maxit, double* x_out, double* E_out) {
     const int N = net->N, n = state_dim(net);
     work_t* W = work_alloc(net);
     int32_t cnt[C_COUNT] = {0};
-    zone_ctx z = {net, rho, T9_0, ln_mult, cnt};
+    zone_ctx z = {net, rho, T9_0, ln_mult, cnt, zeta};
     int nh = 0, rc = 0;
     for (int i = 0; i < N; ++i) W->x1[i] = Y0[i];
     if (net->self_heating) W->x1[N] = T9_0;
@@ -885,14 +903,14 @@ int ora_replay(const ora_network* net, const ora_options* opt, const double* Y0,
    initial-state entries, and (fixed temperature only) T9.  Outputs
    dx [n * P] (row i, column theta) and dE [P], P = R + n + (1 - self_heating). */
 int ora_forward_sensitivity(const ora_network* net, double T9_fixed, double rho,
-                            const double* ln_mult, int32_t S, const double* tape_t,
+                            double zeta, const double* ln_mult, int32_t S, const double* tape_t,
                             const int32_t* tape_k, const double* tape_x,
                             double* dx_out, double* dE_out) {
     const int N = net->N, R = net->R, n = state_dim(net);
     const int P = R + n + (net->self_heating ? 0 : 1);
     work_t* W = work_alloc(net);
     int32_t cnt[C_COUNT] = {0};
-    zone_ctx z = {net, rho, T9_fixed, ln_mult, cnt};
+    zone_ctx z = {net, rho, T9_fixed, ln_mult, cnt, zeta};
     /* history of sensitivity matrices, newest first */
     double* Sh = calloc((size_t)HMAX * n * P, sizeof(double));
     double* SEh = calloc((size_t)HMAX * P, sizeof(double));

@@ -48,11 +48,12 @@ def _topology(spec):
                   Q=_np(getattr(spec, "Q", None), np.float64),
                   scale=_np(getattr(spec, "scale", None), np.float64),
                   ap_pg=_np(getattr(spec, "ap_pg", None), np.int8),
-                  ap_coeffs=_np(getattr(spec, "ap_coeffs", None), np.float64))
+                  ap_coeffs=_np(getattr(spec, "ap_coeffs", None), np.float64),
+                  screen=_np(getattr(spec, "screen", None), np.float64))
     p = lambda a: None if a is None else a.ctypes.data
     topo = _abi.Topology(int(spec.N), int(spec.R), p(arrays["reac"]), p(arrays["prod"]),
                          p(arrays["Q"]), p(arrays["scale"]), int(bool(spec.self_heating)),
-                         p(arrays["ap_pg"]), p(arrays["ap_coeffs"]))
+                         p(arrays["ap_pg"]), p(arrays["ap_coeffs"]), p(arrays["screen"]))
     return arrays, topo, p(arrays["coef"])
 
 
@@ -178,12 +179,14 @@ def burn(net: Network, Y0, T9, rho, t_end: float, rtol: float, atol: float,
          ln_mult=None, *, kernel="persistent", tape: "Optional[Tape]" = None,
          threads_per_block=0, blocks_per_sm=0, blob_in_shared=-1,
          ws_in_shared=-1, max_attempts=500000, time_budget_s=0.0, schedule=None,
-         specialize=0, stream=None, out: Optional[BurnResult] = None):
+         specialize=0, zeta=None, stream=None, out: Optional[BurnResult] = None):
     """Burn Z zones on the GPU.  Y0 [Z,N], T9 [Z], rho [Z] CUDA float64;
     t_end a number, or a CUDA float64 tensor [Z] of per-zone end times;
     ln_mult None, [R] or [Z,R].  specialize: 0/"auto" the kernel generated
     for the network when it qualifies, -1/"generic" the generic kernel, 1..3
-    a specialised storage variant.  Returns BurnResult of CUDA tensors."""
+    a specialised storage variant.  zeta: None or a CUDA float64 tensor [Z]
+    of per-zone plasma parameters (weak screening of a screened network).
+    Returns BurnResult of CUDA tensors."""
     torch = _torch()
     Z = int(Y0.shape[0]) if Y0.dim() == 2 else 0
     _dev(Y0, torch, "Y0", (Z, net.N))
@@ -212,6 +215,9 @@ def burn(net: Network, Y0, T9, rho, t_end: float, rtol: float, atol: float,
         _dev(t_end, torch, "t_end", (Z,))
         o.t_end_zone = t_end.data_ptr()
         t_end = 0.0
+    if zeta is not None:
+        _dev(zeta, torch, "zeta", (Z,))
+        o.zeta_zone = zeta.data_ptr()
     st = stream if stream is not None else torch.cuda.current_stream(dev)
     lib = _abi.load()
     ptr = lambda t: None if t is None else t.data_ptr()
@@ -232,8 +238,8 @@ def burn_multi(sets, t_end: float, rtol: float, atol: float, *, threads_per_bloc
     """Burn several networks' zones in one launch (``nb_burn_multi``).
 
     ``sets``: a list of dicts with keys net, Y0, T9, rho and optionally
-    ln_mult ([R] or [Z, R]) and t_end (a CUDA float64 tensor [Z] of per-zone
-    end times); tensors as for ``burn``.  Returns one BurnResult per set."""
+    ln_mult ([R] or [Z, R]), t_end (a CUDA float64 tensor [Z] of per-zone
+    end times) and zeta ([Z] plasma parameters); tensors as for ``burn``.  Returns one BurnResult per set."""
     torch = _torch()
     if not 1 <= len(sets) <= _abi.MULTI_MAX_SETS:
         raise NetburnError(f"1..{_abi.MULTI_MAX_SETS} sets")
@@ -257,6 +263,9 @@ def burn_multi(sets, t_end: float, rtol: float, atol: float, *, threads_per_bloc
         tz = d.get("t_end")
         if tz is not None:
             _dev(tz, torch, "t_end", (Z,))
+        zt = d.get("zeta")
+        if zt is not None:
+            _dev(zt, torch, "zeta", (Z,))
         dev = Y0.device
         out = BurnResult(torch.empty((Z, net.N), dtype=torch.float64, device=dev),
                          torch.empty((Z,), dtype=torch.float64, device=dev),
@@ -268,6 +277,7 @@ def burn_multi(sets, t_end: float, rtol: float, atol: float, *, threads_per_bloc
         b.Z = Z
         b.Y0, b.T9_0, b.rho = ptr(Y0), ptr(T9), ptr(rho)
         b.ln_mult, b.ln_mult_per_zone, b.t_end_zone = ptr(lm), per_zone, ptr(tz)
+        b.zeta_zone = ptr(zt)
         b.Y, b.T9, b.E = ptr(out.Y), ptr(out.T9), ptr(out.E)
         b.counters, b.status = ptr(out.counters), ptr(out.status)
     o = _options("persistent", threads_per_block, blocks_per_sm, -1, max_attempts,
@@ -308,7 +318,7 @@ class BurnGraph:
 def burn_host(net: Network, Y0, T9, rho, t_end, rtol, atol, ln_mult=None, *,
               kernel="persistent", threads_per_block=0, blocks_per_sm=0,
               blob_in_shared=-1, ws_in_shared=-1, max_attempts=500000,
-              specialize=0, stream=None, out=None):
+              specialize=0, zeta=None, stream=None, out=None):
     """Burn from host (numpy) arrays through ``nb_burn_batch_host``: the
     library copies the inputs in, burns and copies the outputs back.
     Returns a dict of numpy arrays; ``out`` may supply preallocated (e.g.
@@ -326,6 +336,10 @@ def burn_host(net: Network, Y0, T9, rho, t_end, rtol, atol, ln_mult=None, *,
                    status=np.empty(Z, np.int32))
     o = _options(kernel, threads_per_block, blocks_per_sm, blob_in_shared,
                  max_attempts, ws_in_shared, specialize=specialize)
+    if zeta is not None:
+        # per-zone plasma parameters: a device array, as for nb_burn_batch
+        _dev(zeta, torch, "zeta", (Z,))
+        o.zeta_zone = zeta.data_ptr()
     st = stream if stream is not None else torch.cuda.current_stream()
     p = lambda a: None if a is None else a.ctypes.data
     rc = _abi.load().nb_burn_batch_host(

@@ -35,7 +35,7 @@ class Topology(C.Structure):
                 ("reactants", C.c_void_p), ("products", C.c_void_p),
                 ("Q", C.c_void_p), ("scale", C.c_void_p),
                 ("self_heating", C.c_int32), ("ap_pg", C.c_void_p),
-                ("ap_coeffs", C.c_void_p)]
+                ("ap_coeffs", C.c_void_p), ("screen", C.c_void_p)]
 
 
 class NetInfo(C.Structure):
@@ -59,6 +59,7 @@ class BurnSet(C.Structure):
     _fields_ = [("net", C.c_void_p), ("Z", C.c_int64), ("Y0", C.c_void_p),
                 ("T9_0", C.c_void_p), ("rho", C.c_void_p), ("ln_mult", C.c_void_p),
                 ("ln_mult_per_zone", C.c_int32), ("t_end_zone", C.c_void_p),
+                ("zeta_zone", C.c_void_p),
                 ("Y", C.c_void_p), ("T9", C.c_void_p), ("E", C.c_void_p),
                 ("counters", C.c_void_p), ("status", C.c_void_p)]
 
@@ -68,7 +69,8 @@ class Options(C.Structure):
                 ("threads_per_block", C.c_int32), ("blocks_per_sm", C.c_int32),
                 ("blob_in_shared", C.c_int32), ("ws_in_shared", C.c_int32),
                 ("schedule", C.c_int32), ("specialize", C.c_int32),
-                ("t_end_zone", C.c_void_p), ("time_budget_s", C.c_double)]
+                ("t_end_zone", C.c_void_p), ("time_budget_s", C.c_double),
+                ("zeta_zone", C.c_void_p)]
 
 
 def load(build_if_needed: bool = True):

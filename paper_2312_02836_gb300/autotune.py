@@ -44,8 +44,10 @@ DEFAULT_CANDIDATES = GENERIC_CANDIDATES + SPECIALIZED_CANDIDATES
 
 def autotune(net, Y0, T9, rho, t_end, rtol, atol, ln_mult=None, *,
              candidates=DEFAULT_CANDIDATES, key: Optional[str] = None,
-             verbose: bool = False) -> dict:
-    """Return the fastest launch options for burning these zones."""
+             verbose: bool = False, extra: Optional[dict] = None) -> dict:
+    """Return the fastest launch options for burning these zones (extra:
+    further keyword arguments of every burn, e.g. the plasma parameters)."""
+    extra = extra or {}
     import torch
 
     from . import NetburnError, burn
@@ -61,13 +63,13 @@ def autotune(net, Y0, T9, rho, t_end, rtol, atol, ln_mult=None, *,
         candidates = [c for c in candidates if c.get("specialize", 0) < 0]
     for cand in candidates:
         try:
-            out = burn(net, Y0, T9, rho, t_end, rtol, atol, ln_mult, out=out, **cand)
+            out = burn(net, Y0, T9, rho, t_end, rtol, atol, ln_mult, out=out, **cand, **extra)
         except NetburnError:
             continue                      # does not fit this network / GPU
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        burn(net, Y0, T9, rho, t_end, rtol, atol, ln_mult, out=out, **cand)
+        burn(net, Y0, T9, rho, t_end, rtol, atol, ln_mult, out=out, **cand, **extra)
         b.record(stream)
         b.synchronize()
         ms = a.elapsed_time(b)

@@ -101,8 +101,9 @@ __device__ bool adj_init(const Net& t, AdjZone& Zs, const WS& w, const AWS& a,
   s.rho = A.tape.rho[z];
   s.rho2 = s.rho * s.rho;
   s.T9f = A.tape.T9f[z];
+  s.scr = A.tape.scr[z];
   s.lnm = A.lnm ? (A.lnm_per_zone ? A.lnm + (size_t)z * t.R : A.lnm) : nullptr;
-  if (!t.sh) eval_rates(t, s, w, t_powers(s.T9f, true), s.T9f, true);
+  if (!t.sh) eval_rates(t, s, w, t_powers(s.T9f, true, s.scr), s.T9f, true);
   return S == 0;
 }
 
@@ -121,7 +122,7 @@ __device__ bool adj_step(const Net& t, AdjZone& Zs, const WS& w, const AWS& a,
   double alpha[KMAX + 1];
   bdf_alpha(kk, tau, h, alpha);
   for (int i = 0; i < n; ++i) w.x[i] = rs[2 + i];
-  if (t.sh) eval_rates(t, Zs.fz, w, t_powers(w.x[N], true), w.x[N], true);
+  if (t.sh) eval_rates(t, Zs.fz, w, t_powers(w.x[N], true, Zs.fz.scr), w.x[N], true);
   eval_terms(t, w, w.x);
   assemble_M(t, w, w.x, alpha[0], h);
   factor_M(t, w);

@@ -85,6 +85,8 @@ struct BlobHeader {
   int32_t o_ap;         // int32 [R] row of the effective-rate fits, -1 = plain
   int32_t o_apc;        // double [n_ap * 21] (a,p), (p,g), (p,a) fits
   int32_t n_ap;         // effective (alpha,p)(p,gamma) rates
+  int32_t o_scr;        // double [R] weak-screening strengths s_r
+  int32_t has_scr;      // 1 when the network is screened
 };
 
 }  // namespace nb

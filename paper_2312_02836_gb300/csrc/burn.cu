@@ -484,6 +484,7 @@ extern "C" int nb_burn_batch(nb_net net, int64_t Z, const double* Y0, const doub
   if (!(o.time_budget_s >= 0.0)) return NB_E_ARG;
   P.budget_ns = o.time_budget_s > 0.0 ? (unsigned long long)(o.time_budget_s * 1e9) + 1ull : 0ull;
   P.t_end_zone = o.t_end_zone;
+  P.zeta_zone = o.zeta_zone;
   cudaStream_t st = (cudaStream_t)stream;
   std::lock_guard<std::mutex> lk(net->mu);
   if (tape) {
@@ -554,6 +555,7 @@ extern "C" int nb_burn_batch_host(nb_net net, int64_t Z, const double* Y0,
   if (!(o.time_budget_s >= 0.0)) return NB_E_ARG;
   P.budget_ns = o.time_budget_s > 0.0 ? (unsigned long long)(o.time_budget_s * 1e9) + 1ull : 0ull;
   P.t_end_zone = o.t_end_zone;
+  P.zeta_zone = o.zeta_zone;
   rc = launch_burn(net, P, o, st);
   if (rc) return rc;
   CK(cudaMemcpyAsync(Y, b + off_Y, zN, cudaMemcpyDeviceToHost, st));
@@ -584,11 +586,13 @@ extern "C" int nb_tape_alloc(nb_net net, int64_t Z, int32_t max_steps, void** ta
             cudaMalloc(&tp->dev.zstat, (size_t)Z * 4) == cudaSuccess &&
             cudaMalloc(&tp->dev.rho, (size_t)Z * 8) == cudaSuccess &&
             cudaMalloc(&tp->dev.T9f, (size_t)Z * 8) == cudaSuccess &&
+            cudaMalloc(&tp->dev.scr, (size_t)Z * 8) == cudaSuccess &&
             cudaMalloc(&tp->lnm, (size_t)Z * std::max(net->h.R, 1) * 8) == cudaSuccess;
   tp->dev.cap = tp->cap;
   if (!ok) {
     cudaFree(tp->dev.rec); cudaFree(tp->dev.ord); cudaFree(tp->dev.steps);
     cudaFree(tp->dev.zstat); cudaFree(tp->dev.rho); cudaFree(tp->dev.T9f);
+    cudaFree(tp->dev.scr);
     cudaFree(tp->lnm);
     delete tp;
     return NB_E_NOMEM;
@@ -602,6 +606,7 @@ extern "C" int nb_tape_free(void* tape) {
   if (!tp || tp->magic != 0x7a9e5eedu) return NB_E_ARG;
   cudaFree(tp->dev.rec); cudaFree(tp->dev.ord); cudaFree(tp->dev.steps);
   cudaFree(tp->dev.zstat); cudaFree(tp->dev.rho); cudaFree(tp->dev.T9f);
+    cudaFree(tp->dev.scr);
   cudaFree(tp->lnm);
   tp->magic = 0;
   delete tp;

@@ -163,26 +163,36 @@ std::string specialized_source(const std::vector<uint8_t>& blob, int variant) {
   };
   // the full evaluation of k_r (and g_r when `g`), in the generic kernel's
   // order (rate_full)
+  const bool has_scr = h.has_scr != 0;
+  const double* scr = arr<double>(blob, h.o_scr);
+  // screening of the exponent and of d ln k / dT9 (as rate_full does)
+  auto scr_e = [&](int r) { return "fma(" + lit(scr[r]) + ", p.hz, "; };
+  auto dlog = [&](int r, const double* c) {
+    const std::string d = "rate_dlog(" + fit7(c, 1) + ", p)";
+    return has_scr ? "fma(" + lit(scr[r]) + ", p.hzd, " + d + ")" : d;
+  };
   auto emit_full = [&](int r, const char* ind, bool g) {
     const double* a = coef + 7 * r;
     const char* rp = nrho[r] == 0 ? "1.0" : (nrho[r] == 1 ? "s.rho" : "s.rho2");
     o("%se = rate_exponent(%s, p, T9);\n", ind, fit7(a, 0).c_str());
     o("%sif (lnm) e += lnm[%d];\n", ind, r);
+    if (has_scr) o("%se = %se);\n", ind, scr_e(r).c_str());
     if (ap[r] < 0) {
       o("%sw.k[%d] = exp_tang(e) * (%s * %s);\n", ind, r, rp, lit(scale[r]).c_str());
-      if (g) o("%sif (with_g) w.g[%d] = rate_dlog(%s, p);\n", ind, r, fit7(a, 1).c_str());
+      if (g) o("%sif (with_g) w.g[%d] = %s;\n", ind, r, dlog(r, a).c_str());
       return;
     }
     const double* b = apc + 21 * ap[r];
     o("%s{\n%s  double eap = rate_exponent(%s, p, T9);\n", ind, ind, fit7(b, 0).c_str());
     o("%s  if (lnm) eap += lnm[%d];\n", ind, r);
+    if (has_scr) o("%s  eap = %seap);\n", ind, scr_e(r).c_str());
     o("%s  const double epg = rate_exponent(%s, p, T9);\n", ind, fit7(b + 7, 0).c_str());
     o("%s  const double epa = rate_exponent(%s, p, T9);\n", ind, fit7(b + 14, 0).c_str());
     o("%s  const APRate q = ap_rate(e, eap, epg, epa);\n", ind);
     if (g)
-      o("%s  if (with_g)\n%s    w.g[%d] = ap_dlog(q, rate_dlog(%s, p), rate_dlog(%s, p),\n"
+      o("%s  if (with_g)\n%s    w.g[%d] = ap_dlog(q, %s, %s,\n"
         "%s                     rate_dlog(%s, p), rate_dlog(%s, p));\n",
-        ind, ind, r, fit7(a, 1).c_str(), fit7(b, 1).c_str(), ind, fit7(b + 7, 1).c_str(),
+        ind, ind, r, dlog(r, a).c_str(), dlog(r, b).c_str(), ind, fit7(b + 7, 1).c_str(),
         fit7(b + 14, 1).c_str());
     o("%s  w.k[%d] = q.lam * (%s * %s);\n%s}\n", ind, r, rp, lit(scale[r]).c_str(), ind);
   };
@@ -200,7 +210,7 @@ std::string specialized_source(const std::vector<uint8_t>& blob, int variant) {
   o("NB_HD __forceinline__ void eval_rates_near(const GNet&, const Zone& s, GWS& w, double T9,"
     " const TPow& ref, double T9ref) {\n");
   if (sh) {
-    o("  const TPow p = t_powers(T9, false);\n  const DPhi d = delta_phi(p, ref, T9, T9ref);\n"
+    o("  const TPow p = t_powers(T9, false, s.scr);\n  const DPhi d = delta_phi(p, ref, T9, T9ref);\n"
       "  const double* lnm = s.lnm;\n  double de, e;\n");
     for (int r = 0; r < R; ++r) {
       if (ap[r] >= 0) {
@@ -208,6 +218,7 @@ std::string specialized_source(const std::vector<uint8_t>& blob, int variant) {
         continue;
       }
       o("  de = rate_delta(%s, d);\n", fit7(coef + 7 * r, 1).c_str());
+      if (has_scr) o("  de = fma(%s, d.d7, de);\n", lit(scr[r]).c_str());
       o("  if (small_delta(de)) {\n    w.k[%d] = rate_near(w.kp[%d], de);\n  } else {\n", r, r);
       emit_full(r, "    ", false);
       o("  }\n");

@@ -31,6 +31,7 @@ struct Net {
   int n, N, R, sh, hasE, nnz, nd;
   double inv_n;
   const double *coef, *Q, *scale, *rhs_c, *dt_m, *js_c, *rg_c, *apc;
+  const double* scr;   // weak-screening strengths s_r, null without screening
   const int32_t *nrho, *nreac, *rhs_ptr, *js_ptr, *diag_orig, *rg_ptr, *ap;
   const int16_t *reac, *rhs_r, *dt_r, *dt_o, *dt_j, *js_src, *lslot, *uslot, *dslot;
   const int16_t *fw_s, *fw_c, *bw_s, *bw_c, *tfw_s, *tfw_c, *tbw_s, *tbw_c, *rg_i;
@@ -57,6 +58,7 @@ NB_HD inline Net make_net(const unsigned char* b) {
   t.dt_m = at<double>(b, h->o_dt_m); t.js_c = at<double>(b, h->o_js_c);
   t.rg_c = at<double>(b, h->o_rg_c);
   t.apc = at<double>(b, h->o_apc); t.ap = at<int32_t>(b, h->o_ap);
+  t.scr = h->has_scr ? at<double>(b, h->o_scr) : nullptr;
   t.nrho = at<int32_t>(b, h->o_nrho); t.nreac = at<int32_t>(b, h->o_nreac);
   t.rhs_ptr = at<int32_t>(b, h->o_rhs_ptr); t.js_ptr = at<int32_t>(b, h->o_js_ptr);
   t.diag_orig = at<int32_t>(b, h->o_diag_orig); t.rg_ptr = at<int32_t>(b, h->o_rg_ptr);
@@ -142,24 +144,36 @@ NB_HD __forceinline__ double rate_full(const Net& t, const Zone& s, int r, const
   const double* a = t.coef + 7 * r;
   double e = rate_exponent(a[0], a[1], a[2], a[3], a[4], a[5], a[6], p, T9);
   if (s.lnm) e += s.lnm[r];
+  const double sr = t.scr ? t.scr[r] : 0.0;
+  if (t.scr) e = fma(sr, p.hz, e);
   const int nr = t.nrho[r];
   const double rp = nr == 0 ? 1.0 : (nr == 1 ? s.rho : s.rho2);
   const int api = t.ap[r];
   if (api < 0) {
-    if (g) *g = rate_dlog(a[1], a[2], a[3], a[4], a[5], a[6], p);
+    if (g) {
+      *g = rate_dlog(a[1], a[2], a[3], a[4], a[5], a[6], p);
+      if (t.scr) *g = fma(sr, p.hzd, *g);
+    }
     return exp_tang(e) * (rp * t.scale[r]);
   }
   const double* b = t.apc + 21 * api;
   double eap = rate_exponent(b[0], b[1], b[2], b[3], b[4], b[5], b[6], p, T9);
   if (s.lnm) eap += s.lnm[r];
+  if (t.scr) eap = fma(sr, p.hz, eap);
   const double epg = rate_exponent(b[7], b[8], b[9], b[10], b[11], b[12], b[13], p, T9);
   const double epa = rate_exponent(b[14], b[15], b[16], b[17], b[18], b[19], b[20], p, T9);
   const APRate q = ap_rate(e, eap, epg, epa);
-  if (g)
-    *g = ap_dlog(q, rate_dlog(a[1], a[2], a[3], a[4], a[5], a[6], p),
-                 rate_dlog(b[1], b[2], b[3], b[4], b[5], b[6], p),
+  if (g) {
+    double gag = rate_dlog(a[1], a[2], a[3], a[4], a[5], a[6], p);
+    double gap = rate_dlog(b[1], b[2], b[3], b[4], b[5], b[6], p);
+    if (t.scr) {
+      gag = fma(sr, p.hzd, gag);
+      gap = fma(sr, p.hzd, gap);
+    }
+    *g = ap_dlog(q, gag, gap,
                  rate_dlog(b[8], b[9], b[10], b[11], b[12], b[13], p),
                  rate_dlog(b[15], b[16], b[17], b[18], b[19], b[20], p));
+  }
   return q.lam * (rp * t.scale[r]);
 }
 
@@ -182,12 +196,13 @@ NB_HD inline void eval_rates(const Net& t, const Zone& s, const WS& w, const TPo
 // Effective (alpha,p)(p,gamma) rates always take the full evaluation.
 NB_HD inline void eval_rates_near(const Net& t, const Zone& s, const WS& w, double T9,
                                   const TPow& ref, double T9ref) {
-  const TPow p = t_powers(T9, false);
+  const TPow p = t_powers(T9, false, s.scr);
   const DPhi d = delta_phi(p, ref, T9, T9ref);
 #pragma unroll 2
   for (int r = 0; r < t.R; ++r) {
     const double* a = t.coef + 7 * r;
-    const double de = rate_delta(a[1], a[2], a[3], a[4], a[5], a[6], d);
+    double de = rate_delta(a[1], a[2], a[3], a[4], a[5], a[6], d);
+    if (t.scr) de = fma(t.scr[r], d.d7, de);
     if (t.ap[r] < 0 && small_delta(de)) w.k[r] = rate_near(w.kp[r], de);
     else w.k[r] = rate_full(t, s, r, p, T9, nullptr);
   }

@@ -63,6 +63,7 @@ struct TapeDev {
   int32_t* zstat;    // [Z] status the zone finished with
   double* rho;       // [Z]
   double* T9f;       // [Z] fixed temperature (or initial T9)
+  double* scr;       // [Z] screening factor sqrt(rho zeta) 10^-4.5 of the zone
   int32_t cap;
 };
 
@@ -85,12 +86,14 @@ struct BurnParams {
   unsigned long long budget_ns;  // watchdog budget per block, 0 = none
   const int32_t* order;       // claim order (zone index per claim), or null
   const double* t_end_zone;   // [Z] per-zone end time (operator split), or null
+  const double* zeta_zone;    // [Z] plasma parameter for screening, or null
 };
 
 // Register state of the zone a lane is integrating.
 struct Zone {
   long long z;
   double t, h, E, T9f, rho, rho2, tend;
+  double scr;                 // sqrt(rho zeta) 10^-4.5: H_r = s_r scr T9^(-3/2)
   const double* lnm;
   int k, nh, hh, nconsec, nfail, status;
   int c_acc, c_rej_err, c_rej_newton, c_newton, c_jac, c_rhs, c_teval, c_edot;
@@ -126,9 +129,11 @@ NB_HD __forceinline__ bool finite_bits(double v) {
 // Powers of T9 in the rate fit (and their T9-derivative factors)
 struct TPow {
   double t13, iT, t23, it13, T53, lnT, d1, d2, d3, d5;
+  double hz, hzd;   // screening: scr T9^(-3/2) and its T9-derivative factor
 };
 
-NB_HD __forceinline__ TPow t_powers(double T9, bool with_g) {
+// scr: the zone's screening factor (0 without screening)
+NB_HD __forceinline__ TPow t_powers(double T9, bool with_g, double scr) {
   TPow p;
   p.t13 = cbrt(T9);
   p.iT = 1.0 / T9;
@@ -142,6 +147,13 @@ NB_HD __forceinline__ TPow t_powers(double T9, bool with_g) {
     p.d2 = (-1.0 / 3.0) * p.iT * p.it13;
     p.d3 = (1.0 / 3.0) * p.it13 * p.it13;
     p.d5 = (5.0 / 3.0) * p.t23;
+  }
+  // weak screening H_r = s_r sqrt(rho zeta) T6^(-3/2) = s_r hz, T6 = 1e3 T9;
+  // dH_r/dT9 = -1.5 H_r / T9 = s_r hzd
+  p.hz = p.hzd = 0.0;
+  if (scr != 0.0) {
+    p.hz = scr * (p.iT * sqrt(p.iT));
+    if (with_g) p.hzd = -1.5 * p.hz * p.iT;
   }
   return p;
 }
@@ -208,7 +220,7 @@ NB_HD __forceinline__ double ap_dlog(const APRate& a, double g_ag, double g_ap, 
 // the same as when it is formed whole, so the rates are as accurate as the
 // full evaluation's.  A larger de takes the full evaluation.
 struct DPhi {
-  double d1, d2, d3, d4, d5, d6;
+  double d1, d2, d3, d4, d5, d6, d7;   // d7: change of the screening term hz
 };
 
 NB_HD __forceinline__ DPhi delta_phi(const TPow& p, const TPow& r, double T9, double T9r) {
@@ -219,6 +231,7 @@ NB_HD __forceinline__ DPhi delta_phi(const TPow& p, const TPow& r, double T9, do
   d.d4 = T9 - T9r;
   d.d5 = p.T53 - r.T53;
   d.d6 = p.lnT - r.lnT;
+  d.d7 = p.hz - r.hz;
   return d;
 }
 
@@ -451,11 +464,13 @@ NB_HD __forceinline__ bool zone_init(const NT& t, Zone& s, WT& w, const BurnPara
   s.T9f = P.T9_0[z];
   s.rho = P.rho[z];
   s.rho2 = s.rho * s.rho;
+  const double zeta = P.zeta_zone ? P.zeta_zone[z] : 0.0;
+  s.scr = zeta > 0.0 ? sqrt(s.rho * zeta) * 3.1622776601683794e-05 : 0.0;   // 10^-4.5
   s.lnm = P.lnm ? (P.lnm_per_zone ? P.lnm + (unsigned long long)z * t.R : P.lnm) : nullptr;
   s.tend = P.t_end_zone ? P.t_end_zone[z] : P.t_end;
   auto& x0 = w.xh;  // history slot 0
   bool fin = finite_bits(s.T9f) && s.T9f > 0.0 && finite_bits(s.rho) &&
-             finite_bits(s.tend) && s.tend >= 0.0;
+             finite_bits(s.tend) && s.tend >= 0.0 && finite_bits(zeta) && zeta >= 0.0;
   NB_UNROLL
   for (int i = 0; i < N; ++i) {
     const double y = P.Y0[(unsigned long long)z * N + i];
@@ -469,9 +484,10 @@ NB_HD __forceinline__ bool zone_init(const NT& t, Zone& s, WT& w, const BurnPara
     P.tape.steps[z] = 0;
     P.tape.rho[z] = s.rho;
     P.tape.T9f[z] = s.T9f;
+    P.tape.scr[z] = s.scr;
     tape_record(t, P, s, x0, 0.0, 0);
   }
-  eval_rates(t, s, w, t_powers(s.T9f, false), s.T9f, false);
+  eval_rates(t, s, w, t_powers(s.T9f, false, s.scr), s.T9f, false);
   s.c_teval++;
   eval_terms(t, w, x0);
   eval_f(t, w, x0, w.f0);
@@ -499,7 +515,7 @@ NB_HD __forceinline__ bool zone_init(const NT& t, Zone& s, WT& w, const BurnPara
   for (int i = 0; i < n; ++i) w.x[i] = fma(hp, w.f0[i], x0[i]);
   if (t.sh) {
     const double T9 = w.x[N];
-    eval_rates(t, s, w, t_powers(T9, false), T9, false);
+    eval_rates(t, s, w, t_powers(T9, false, s.scr), T9, false);
     s.c_teval++;
   }
   eval_terms(t, w, w.x);
@@ -575,7 +591,7 @@ NB_HD __forceinline__ bool zone_attempt(const NT& t, Zone& s, WT& w, const BurnP
   double Tref = 0.0;
   if (t.sh) {
     Tref = w.x[N];
-    pref = t_powers(Tref, true);
+    pref = t_powers(Tref, true, s.scr);
     eval_rates(t, s, w, pref, Tref, true);
     save_ref_rates(t, w);
     s.c_teval++;

@@ -155,6 +155,7 @@ extern "C" int nb_burn_multi(int32_t n_sets, const nb_burn_set* sets, double t_e
     P.Y = b.Y; P.T9 = b.T9; P.E = b.E; P.counters = b.counters; P.status = b.status;
     P.max_attempts = o.max_attempts;
     P.t_end_zone = b.t_end_zone;
+    P.zeta_zone = b.zeta_zone;
   }
   M.off[n_sets] = off;
   // the first set's network lends its workspace and queue counter

@@ -290,6 +290,12 @@ int build_blob(const nb_topology* T, const double* coeffs,
     }
   }
   const int n_ap = (int)(apc.size() / 21);
+  std::vector<double> scr(R > 0 ? R : 1, 0.0);
+  if (T->screen)
+    for (int r = 0; r < R; ++r) {
+      if (!std::isfinite(T->screen[r]) || T->screen[r] < 0.0) return NB_E_ARG;
+      scr[r] = T->screen[r];
+    }
   if (apc.empty()) apc.push_back(0.0);
   std::vector<double> Q(R, 0.0), scale(R, 1.0);
   for (int r = 0; r < R; ++r) {
@@ -307,6 +313,8 @@ int build_blob(const nb_topology* T, const double* coeffs,
   h.o_ap = B.add(ap);
   h.o_apc = B.add(apc);
   h.n_ap = n_ap;
+  h.o_scr = B.add(scr);
+  h.has_scr = T->screen ? 1 : 0;
   h.o_Q = B.add(Q);
   h.o_scale = B.add(scale);
   h.o_nrho = B.add(nrho);
@@ -373,7 +381,8 @@ int build_blob(const nb_topology* T, const double* coeffs,
   }
   // powers of T9, 7-term exponents, k_r; an effective rate adds three
   // exponents and their combination
-  h.fl_teval = 2 + 14 * (int64_t)R + 45 * (int64_t)n_ap;
+  h.fl_teval = 2 + 14 * (int64_t)R + 45 * (int64_t)n_ap +
+               (T->screen ? 3 + 2 * (int64_t)(R + n_ap) : 0);
   h.fl_teval_g = 6 + 10 * (int64_t)R + 38 * (int64_t)n_ap;  // d ln lambda / dT9
   h.fl_terms = terms;                        // R_r = k_r prod Y
   h.fl_rhs = 2 * (int64_t)rhs_r.size() + (sh ? 2 * (int64_t)R + N + 5 : 0);

@@ -91,3 +91,22 @@ def test_effective_rates_in_the_source_and_checked_on_load():
             spec.ap_coeffs[4, 1, 2] = float("nan")
         arrays, topo, coef = nb._topology(spec)
         assert lib.nb_specialize_source(C.byref(topo), coef, 0, None, 0, C.byref(n)) == -1
+
+
+def test_screening_in_the_source():
+    # a screened network adds s_r * hz to every exponent (full and near
+    # evaluations) and s_r * hzd to every d ln k / dT9
+    net = gen.network("chain13_heat_scr")
+    src = nb.specialized_source(net, 0)
+    assert src.count(", p.hz, e);") == 2 * net.R      # full, and near's fallback
+    assert src.count(", d.d7, de);") == net.R
+    assert src.count(", p.hzd, rate_dlog(") == net.R
+    assert "p.hz" not in nb.specialized_source(gen.network("chain13_heat"), 0)
+    # a negative strength is rejected on the host
+    spec = gen.network("chain13_heat_scr")
+    spec.screen = spec.screen.copy()
+    spec.screen[2] = -1.0
+    arrays, topo, coef = nb._topology(spec)
+    n = C.c_int64()
+    assert _abi.load().nb_specialize_source(C.byref(topo), coef, 0, None, 0,
+                                            C.byref(n)) == -1

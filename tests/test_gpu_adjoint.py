@@ -22,11 +22,12 @@ def _forward_sens(net, z, s, zones, ln_mult=None):
     out = []
     for i in zones:
         lm = None if ln_mult is None else ln_mult
+        zeta = float(z["zeta"][i]) if "zeta" in z else 0.0
         tp = oracle.burn_tape(net, z["Y"][i], z["T9"][i], z["rho"][i], s["t_end"],
-                              s["rtol"], s["atol"], ln_mult=lm)
+                              s["rtol"], s["atol"], ln_mult=lm, zeta=zeta)
         assert tp["status"] == 0
         dx, dE = oracle.forward_sensitivity(net, z["T9"][i], z["rho"][i], tp["t"],
-                                            tp["k"], tp["x"], ln_mult=lm)
+                                            tp["k"], tp["x"], ln_mult=lm, zeta=zeta)
         out.append((dx, dE, int(tp["counters"][0])))
     return out
 
@@ -39,7 +40,7 @@ def _gpu_adjoint(nb, torch, net, z, s, gY, gE, gT9, ln_mult=None, max_steps=2000
     lm = None if ln_mult is None else torch.from_numpy(ln_mult).to(dev)
     fw = nb.burn(nc, torch.from_numpy(z["Y"]).to(dev), torch.from_numpy(z["T9"]).to(dev),
                  torch.from_numpy(z["rho"]).to(dev), s["t_end"], s["rtol"], s["atol"], lm,
-                 tape=tape)
+                 tape=tape, zeta=torch.from_numpy(z["zeta"]).to(dev) if "zeta" in z else None)
     t = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     dl, dY0, dT0 = nb.adjoint(nc, tape, t(gY), t(gE), t(gT9))
     torch.cuda.synchronize()
@@ -57,13 +58,15 @@ def _check(expect, got, rtol, scale=None, out_mag=0.0, abs_floor=0.0):
     assert not bad.any(), (np.where(bad), got[bad][:4], expect[bad][:4])
 
 
-@pytest.mark.parametrize("name,Z", [("net48_adjoint", 24), ("chain13_heat", 48)])
+@pytest.mark.parametrize("name,Z", [("net48_adjoint", 24), ("chain13_heat", 48),
+                                    ("chain13_heat_scr", 32)])
 def test_adjoint_matches_forward_sensitivity(name, Z):
     nb, torch = nb_mod()
     net, z, s = gen.problem(name, Z)
     n = net.N + (1 if net.self_heating else 0)
     # cotangents: E, and the 5 largest final abundances of each zone (one-hot)
-    o = oracle.burn(net, z["Y"], z["T9"], z["rho"], s["t_end"], s["rtol"], s["atol"])
+    o = oracle.burn(net, z["Y"], z["T9"], z["rho"], s["t_end"], s["rtol"], s["atol"],
+                    zeta=z.get("zeta"))
     top = gen.largest_species(o["Y"], 5)
     K = 6
     gY = np.zeros((K, Z, net.N))

@@ -30,7 +30,7 @@ def oracle_run(name, Z, sel=None, **kw):
             z = {k: v[sel] for k, v in z.items()}
         s.update(kw)
         _ORACLE[key] = oracle.burn(net, z["Y"], z["T9"], z["rho"], s["t_end"],
-                                   s["rtol"], s["atol"])
+                                   s["rtol"], s["atol"], zeta=z.get("zeta"))
     return _ORACLE[key]
 
 
@@ -42,13 +42,15 @@ def gpu_run(nb, torch, net_c, z, s, **kw):
     lm = kw.pop("ln_mult", None)
     if lm is not None:
         lm = torch.from_numpy(np.ascontiguousarray(lm)).to(dev)
+    if "zeta" in z:
+        kw["zeta"] = torch.from_numpy(z["zeta"]).to(dev)
     out = nb.burn(net_c, Y0, T9, rho, s["t_end"], s["rtol"], s["atol"], lm, **kw)
     torch.cuda.synchronize()
     return to_numpy(out)
 
 
 CASES = [("chain13", 4096), ("chain13_literal", 1024), ("chain13_heat", 2048),
-         ("chain13_heat_ap", 2048),
+         ("chain13_heat_ap", 2048), ("chain13_heat_scr", 2048),
          ("net48", 256), ("net48_adjoint", 128), ("net128_heat", 16)]
 
 

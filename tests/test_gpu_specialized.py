@@ -29,7 +29,7 @@ def _equal(a, b):
 
 
 CASES = [("chain13", 2048), ("chain13_literal", 1024), ("chain13_heat", 2048),
-         ("chain13_heat_ap", 1024)]
+         ("chain13_heat_ap", 1024), ("chain13_heat_scr", 1024)]
 
 
 @pytest.mark.parametrize("variant", [1, 2, 3])
@@ -38,9 +38,10 @@ def test_specialized_equals_generic_bitwise(name, Z, variant):
     nb, torch, net, z, s, t = _setup(name, Z)
     nc = nb.Network(net)
     args = (nc, t["Y"], t["T9"], t["rho"], s["t_end"], s["rtol"], s["atol"])
-    ref = nb.burn(*args, specialize="generic")
+    zk = dict(zeta=t["zeta"]) if "zeta" in t else {}
+    ref = nb.burn(*args, specialize="generic", **zk)
     assert nc.info()["last_specialized"] == 0
-    out = nb.burn(*args, specialize=variant)
+    out = nb.burn(*args, specialize=variant, **zk)
     torch.cuda.synchronize()
     assert nc.info()["last_specialized"] == variant
     assert int((out.status == 0).sum()) == Z
@@ -48,7 +49,7 @@ def test_specialized_equals_generic_bitwise(name, Z, variant):
     # other launch shapes of the specialised kernel: the same bits
     for tpb, bps in ((64, 1), (128, 2), (256, 1)):
         again = nb.burn(*args, specialize=variant, threads_per_block=tpb,
-                        blocks_per_sm=bps, schedule="fifo")
+                        blocks_per_sm=bps, schedule="fifo", **zk)
         torch.cuda.synchronize()
         _equal(again, ref)
 

@@ -75,6 +75,52 @@ def test_rate_temperature_derivative_fd():
         np.testing.assert_allclose(g, fd, rtol=1e-6, atol=1e-8 * np.abs(g).max())
 
 
+# ---------------------------------------------------------------- screening
+
+def test_screening_factor_closed_form_and_zero_zeta():
+    # alpha + alpha (s = 0.188 * 2 * 2) at T9 = 1 (T6 = 1000):
+    # k_screened / k = exp(s sqrt(rho zeta) 1000^(-3/2))
+    net = make_net([(0, 0)], [(1,)], N=2, lam=[3.0])
+    net.screen = np.array([0.188 * 4.0])
+    rho, zeta = 1e6, 1.5
+    k0, _ = oracle.rate_factors(net, 1.0, rho)
+    k, _ = oracle.rate_factors(net, 1.0, rho, zeta=zeta)
+    H = 0.188 * 4.0 * math.sqrt(rho * zeta) * 1000.0 ** -1.5
+    np.testing.assert_allclose(k / k0, [math.exp(H)], rtol=1e-14)
+    k00, _ = oracle.rate_factors(net, 1.0, rho, zeta=0.0)
+    np.testing.assert_array_equal(k00, k0)
+
+
+def test_screening_coefficient_is_debye_hueckel():
+    # Weak screening: H = Z1 Z2 e^2 / (k T lambda_D) with the Debye length
+    # lambda_D = sqrt(k T / (4 pi e^2 rho N_A zeta)), in cgs units with
+    # CODATA constants.  The oracle's H for s = 0.188 Z1 Z2 (T6 = 1e3 T9)
+    # must match it to the 3 digits of 0.188.
+    e, kB, NA = 4.80320471e-10, 1.380649e-16, 6.02214076e23
+    net = make_net([(0, 1)], [(2,)], N=3, lam=[1.0])
+    Z1, Z2 = 6.0, 2.0
+    net.screen = np.array([0.188 * Z1 * Z2])
+    for T9, rho, zeta in ((0.3, 1e7, 0.8), (2.0, 1e5, 3.0)):
+        k0, _ = oracle.rate_factors(net, T9, rho)
+        k, _ = oracle.rate_factors(net, T9, rho, zeta=zeta)
+        T = T9 * 1e9
+        lam_D = math.sqrt(kB * T / (4 * math.pi * e ** 2 * rho * NA * zeta))
+        H = Z1 * Z2 * e ** 2 / (kB * T * lam_D)
+        assert abs(math.log(k[0] / k0[0]) / H - 1) < 2e-3
+
+
+def test_screened_rate_temperature_derivative_fd():
+    net, z, s = gen.problem("chain13_heat_scr", 8)
+    for i in range(4):
+        T9, rho, zeta = z["T9"][i], z["rho"][i], z["zeta"][i]
+        _, g = oracle.rate_factors(net, T9, rho, zeta=zeta)
+        h = 1e-6 * T9
+        kp, _ = oracle.rate_factors(net, T9 + h, rho, zeta=zeta)
+        km, _ = oracle.rate_factors(net, T9 - h, rho, zeta=zeta)
+        fd = (np.log(kp) - np.log(km)) / (2 * h)
+        np.testing.assert_allclose(g, fd, rtol=1e-6, atol=1e-8 * np.abs(g).max())
+
+
 # ------------------------------------------ effective (alpha,p)(p,gamma) rate
 
 def _ap_net(lams, reac=((0, 1),), prod=((2,),), N=3, scale=None):
