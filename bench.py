@@ -154,9 +154,11 @@ def sampled_parity(name, net, z, s, out, n) -> dict:
         # FP64 noise floor: which attempts converge there is decided by rounding
         keep = o["counters"][:, 2] == 0
     try:
+        from tests.parity import TABULATED
+        bar = TABULATED if getattr(net, "tab_of", None) is not None else {}
         rep = compare({k: v[keep] for k, v in g.items()},
                       {k: o[k][keep] for k in ("Y", "T9", "E", "counters", "status")},
-                      s["atol"])
+                      s["atol"], rtol=s["rtol"], **bar)
         rep["passed"] = True
     except AssertionError as e:
         rep = {"passed": False, "error": str(e)[:300]}

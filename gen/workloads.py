@@ -64,6 +64,15 @@ CONFIGS = {
                              T9=(0.5, 5.0), rho=(1e5, 1e8), t_end=1e-3,
                              rtol=1e-8, atol=1e-12, zone_seed=1001, Q=True,
                              screen=True, zeta=(1.0, 2.0)),
+    # The self-heating chain with reactions 0..5 (triple-alpha and the first
+    # five captures) given as tables (TabularRate,
+    # the paper's Sec. 2: rates tabulated in (rho Ye, T)): each table is its
+    # fit's ln lambda at the grid's temperatures plus a density slope and
+    # noise, on a 5 x 12 grid in (log10 rho Ye, T9); charges Z_i = A_i / 2.
+    "chain13_heat_tab": dict(kind="chain", literal=False, heat=True, Z=65536,
+                             T9=(0.5, 5.0), rho=(1e5, 1e8), t_end=1e-3,
+                             rtol=1e-8, atol=1e-12, zone_seed=1001, Q=True,
+                             tab=(0, 6)),
     # Random sparse network, 48 species / 180 rates, fixed T and rho.
     "net48": dict(kind="random", N=48, mix=(60, 100, 20), topo_seed=2,
                   heat=False, Z=262144, T9=(0.3, 6.0), rho=(1e4, 1e9),
@@ -104,6 +113,14 @@ class NetworkSpec:
     # weak-screening strength per reaction, s_r = 0.188 sum Z_a Z_b over the
     # reactants' successive pairs, or None
     screen: Optional[np.ndarray] = None
+    # tabulated rates: tab_of [R] (table of reaction r, -1 = its fit), the
+    # grid tab_dens [nd] (log10 rho Ye) x tab_t9 [nt], tab_lnl [n_tab, nd, nt]
+    # (ln lambda at the nodes), charge [N] (Ye = sum Z_i Y_i)
+    tab_of: Optional[np.ndarray] = None
+    tab_dens: Optional[np.ndarray] = None
+    tab_t9: Optional[np.ndarray] = None
+    tab_lnl: Optional[np.ndarray] = None
+    charge: Optional[np.ndarray] = None
     extra: dict = field(default_factory=dict)
 
 
@@ -133,6 +150,29 @@ def _screen_strengths(reac: np.ndarray, charge: np.ndarray) -> np.ndarray:
             zsum += zb
         out[r] = 0.188 * acc
     return out
+
+
+TAB_DENS = np.array([4.0, 5.0, 6.0, 7.0, 8.0])                  # log10(rho Ye)
+TAB_T9 = np.array([0.3, 0.5, 0.7, 1.0, 1.5, 2.0, 3.0, 4.0, 5.0, 6.0, 8.0, 10.0])
+
+
+def _tables(coeffs: np.ndarray, rows, R: int) -> dict:
+    """Synthetic rate tables for reactions ``rows``: the fit's exponent at
+    each grid temperature, plus 0.25 (log10 rho Ye - 6) and N(0, 0.1) noise
+    per node (its own seed)."""
+    rng = np.random.Generator(np.random.PCG64(6))
+    rows = list(rows)
+    tab_of = np.full(R, -1, dtype=np.int32)
+    lnl = np.empty((len(rows), TAB_DENS.size, TAB_T9.size))
+    T = TAB_T9
+    phi = np.stack([np.ones_like(T), 1 / T, T ** (-1 / 3), T ** (1 / 3), T, T ** (5 / 3),
+                    np.log(T)])
+    for m, r in enumerate(rows):
+        tab_of[r] = m
+        base = coeffs[r] @ phi
+        lnl[m] = (base[None, :] + 0.25 * (TAB_DENS[:, None] - 6.0)
+                  + rng.normal(0.0, 0.1, (TAB_DENS.size, T.size)))
+    return dict(tab_of=tab_of, tab_dens=TAB_DENS.copy(), tab_t9=TAB_T9.copy(), tab_lnl=lnl)
 
 
 def _pad3(t):
@@ -252,10 +292,14 @@ def network(name: str) -> NetworkSpec:
         screen = None
         if cfg.get("screen"):
             screen = _screen_strengths(reac, ALPHA_CHAIN_A / 2.0)
+        tab = {}
+        if cfg.get("tab") is not None:
+            tab = _tables(coeffs, range(*cfg["tab"]), R)
+            tab["charge"] = ALPHA_CHAIN_A / 2.0
         return NetworkSpec(name=name, N=13, R=R, reactants=reac, products=prod,
                            A=ALPHA_CHAIN_A.copy(), coeffs=coeffs, Q=Q,
                            self_heating=cfg["heat"], seed_used=0,
-                           ap_pg=ap_pg, ap_coeffs=ap_coeffs, screen=screen)
+                           ap_pg=ap_pg, ap_coeffs=ap_coeffs, screen=screen, **tab)
     N = cfg["N"]
     seed = cfg["topo_seed"]
     while True:

@@ -106,6 +106,21 @@ typedef struct {
    * pairs.  zeta, the plasma parameter sum (Z_i^2 + Z_i) Y_i, is a per-zone
    * input (nb_options.zeta_zone) held over the burn. */
   const double* screen;
+  /* Tabulated rates (Sec. 2: TabularRate, weak rates tabulated in
+   * (rho Ye, T)).  tab_of [R] or NULL: the table of reaction r, -1 = its
+   * fit; tables 0..n_tab-1 share one grid of tab_nd density nodes tab_dens
+   * [tab_nd] (log10(rho Ye), increasing) and tab_nt temperature nodes tab_t9
+   * [tab_nt] (T9, increasing), and hold ln lambda at the nodes in tab_lnl
+   * [n_tab, tab_nd, tab_nt].  ln lambda is bilinear in (log10 rho Ye, T9)
+   * between nodes and clamped to the grid's edges.  charge [N] (required
+   * with tables): Z_i; Ye = sum Z_i Y_i of the zone's initial composition,
+   * held over the burn.  A reaction is tabulated or effective, not both. */
+  const int32_t* tab_of;
+  int32_t tab_nd, tab_nt;
+  const double* tab_dens;
+  const double* tab_t9;
+  const double* tab_lnl;
+  const double* charge;
 } nb_topology;
 
 typedef struct {

@@ -52,7 +52,10 @@ class _Net(C.Structure):
                 ("reactants", C.c_void_p), ("products", C.c_void_p),
                 ("Q", C.c_void_p), ("scale", C.c_void_p), ("coeffs", C.c_void_p),
                 ("ap_pg", C.c_void_p), ("ap_coeffs", C.c_void_p),
-                ("screen", C.c_void_p)]
+                ("screen", C.c_void_p), ("tab_of", C.c_void_p),
+                ("tab_nd", C.c_int32), ("tab_nt", C.c_int32),
+                ("tab_dens", C.c_void_p), ("tab_t9", C.c_void_p),
+                ("tab_lnl", C.c_void_p), ("charge", C.c_void_p)]
 
 
 class _Opt(C.Structure):
@@ -68,9 +71,9 @@ def _load():
         if _lib is None:
             lib = C.CDLL(build())
             P, I32, I64, D = C.c_void_p, C.c_int32, C.c_int64, C.c_double
-            lib.ora_rate_factors.argtypes = [P, D, D, D, P, P, P]
-            lib.ora_rhs.argtypes = [P, P, D, D, D, P, P, P]
-            lib.ora_jacobian.argtypes = [P, P, D, D, D, P, P]
+            lib.ora_rate_factors.argtypes = [P, D, D, D, D, P, P, P]
+            lib.ora_rhs.argtypes = [P, P, D, D, D, D, P, P, P]
+            lib.ora_jacobian.argtypes = [P, P, D, D, D, D, P, P]
             lib.ora_bdf_alpha.argtypes = [I32, D, P, D, P]
             lib.ora_extrapolate.argtypes = [I32, I32, P, P, D, P]
             lib.ora_burn_batch.argtypes = [P, P, I64, P, P, P, P, I32, P, P, P,
@@ -112,6 +115,17 @@ class Network:
         self.ap_pg = None if ap is None else np.ascontiguousarray(ap, dtype=np.int8)
         self.ap_coeffs = _f64(getattr(spec, "ap_coeffs", None))
         self.screen = _f64(getattr(spec, "screen", None))
+        tab = getattr(spec, "tab_of", None)
+        self.tab_of = None if tab is None else np.ascontiguousarray(tab, dtype=np.int32)
+        self.tab_dens = _f64(getattr(spec, "tab_dens", None))
+        self.tab_t9 = _f64(getattr(spec, "tab_t9", None))
+        self.tab_lnl = _f64(getattr(spec, "tab_lnl", None))
+        self.charge = _f64(getattr(spec, "charge", None))
+        if self.tab_of is not None:
+            if self.tab_lnl is None or self.charge is None:
+                raise ValueError("tab_of needs tab_dens, tab_t9, tab_lnl and charge")
+            if self.ap_pg is not None and ((self.tab_of >= 0) & (self.ap_pg != 0)).any():
+                raise ValueError("a reaction is either tabulated or effective")
         if self.ap_pg is not None and (self.ap_coeffs is None
                                        or self.ap_coeffs.size != 21 * self.R):
             raise ValueError("ap_pg needs ap_coeffs [R, 3, 7]")
@@ -121,7 +135,11 @@ class Network:
         self._s = _Net(self.N, self.R, int(self.self_heating),
                        _p(self.reactants), _p(self.products), _p(self.Q),
                        _p(self.scale), _p(self.coeffs), _p(self.ap_pg),
-                       _p(self.ap_coeffs), _p(self.screen))
+                       _p(self.ap_coeffs), _p(self.screen), _p(self.tab_of),
+                       0 if self.tab_dens is None else self.tab_dens.size,
+                       0 if self.tab_t9 is None else self.tab_t9.size,
+                       _p(self.tab_dens), _p(self.tab_t9), _p(self.tab_lnl),
+                       _p(self.charge))
 
     @property
     def ptr(self):
@@ -138,19 +156,21 @@ def _opts(t_end, rtol, atol, max_attempts=500000, newton_tol=1e-3,
                 fixed_h, fixed_order, max_order)
 
 
-def rate_factors(net, T9, rho, ln_mult=None, zeta=0.0):
+def rate_factors(net, T9, rho, ln_mult=None, zeta=0.0, ye=1.0):
     """k_r = s_r e^p_r rho^(n_r-1) lambda_r(T9) exp(H_r) and d ln k_r / dT9
-    (H_r the weak-screening exponent at plasma parameter zeta)."""
+    (H_r the weak-screening exponent at plasma parameter zeta; tabulated
+    rates read at log10(rho ye))."""
     net = _net(net)
     lib = _load()
     k = np.empty(net.R)
     g = np.empty(net.R)
     lm = _f64(ln_mult)
-    lib.ora_rate_factors(net.ptr, float(T9), float(rho), float(zeta), _p(lm), _p(k), _p(g))
+    lib.ora_rate_factors(net.ptr, float(T9), float(rho), float(zeta), float(ye), _p(lm),
+                         _p(k), _p(g))
     return k, g
 
 
-def rhs(net, x, T9=0.0, rho=1.0, ln_mult=None, zeta=0.0):
+def rhs(net, x, T9=0.0, rho=1.0, ln_mult=None, zeta=0.0, ye=1.0):
     """f(x) [n] and edot at state x (x[N] is T9 under self-heating)."""
     net = _net(net)
     lib = _load()
@@ -158,19 +178,20 @@ def rhs(net, x, T9=0.0, rho=1.0, ln_mult=None, zeta=0.0):
     f = np.empty(net.n)
     ed = C.c_double(0.0)
     lm = _f64(ln_mult)
-    lib.ora_rhs(net.ptr, _p(x), float(T9), float(rho), float(zeta), _p(lm), _p(f),
+    lib.ora_rhs(net.ptr, _p(x), float(T9), float(rho), float(zeta), float(ye), _p(lm), _p(f),
                 C.byref(ed))
     return f, ed.value
 
 
-def jacobian(net, x, T9=0.0, rho=1.0, ln_mult=None, zeta=0.0):
+def jacobian(net, x, T9=0.0, rho=1.0, ln_mult=None, zeta=0.0, ye=1.0):
     """Analytic Jacobian df/dx [n, n]."""
     net = _net(net)
     lib = _load()
     x = _f64(x)
     J = np.empty((net.n, net.n))
     lm = _f64(ln_mult)
-    lib.ora_jacobian(net.ptr, _p(x), float(T9), float(rho), float(zeta), _p(lm), _p(J))
+    lib.ora_jacobian(net.ptr, _p(x), float(T9), float(rho), float(zeta), float(ye), _p(lm),
+                     _p(J))
     return J
 
 

@@ -23,6 +23,11 @@
  *               s_r = 0.188 sum Z_a Z_b over the reactants' successive pairs
  *               (given per reaction) and zeta the zone's plasma parameter
  *               sum (Z_i^2 + Z_i) Y_i, an input of the zone held over its burn
+ *   tabulated   a reaction given as a table (TabularRate, Sec. 2: weak rates
+ *               tabulated in (rho Ye, T)) takes ln lambda by bilinear
+ *               interpolation in (log10(rho Ye), T9) on a rectilinear grid,
+ *               clamped to the grid's edges; Ye = sum Z_i Y_i of the zone's
+ *               initial composition, held over the burn
  *   effective   a reaction flagged as the (alpha,p)(p,gamma) approximation of
  *               Sec. 2 (A(a,p)X(p,g)B merged into one A(a,g)B rate, valid
  *               when proton capture on X is fast, so that the proton flow
@@ -101,6 +106,12 @@ typedef struct {
     const int8_t* ap_pg;        /* [R] or NULL: 1 = (alpha,p)(p,gamma) effective */
     const double* ap_coeffs;    /* [R*21] fits of (a,p), (p,g), (p,a), or NULL */
     const double* screen;       /* [R] weak-screening strengths s_r, or NULL */
+    const int32_t* tab_of;      /* [R] table of reaction r (-1: fit), or NULL */
+    int32_t tab_nd, tab_nt;     /* grid: density and temperature nodes */
+    const double* tab_dens;     /* [tab_nd] log10(rho Ye) nodes, increasing */
+    const double* tab_t9;       /* [tab_nt] T9 nodes, increasing */
+    const double* tab_lnl;      /* [n_tab * tab_nd * tab_nt] ln lambda at the nodes */
+    const double* charge;       /* [N] species charges Z_i (for Ye), or NULL */
 } ora_network;
 
 typedef struct {
@@ -134,8 +145,36 @@ static double stoich(const ora_network* net, int i, int r) {
 }
 
 /* k_r = s_r e^(p_r) rho^(n_r-1) lambda_r(T9) and g_r = d ln lambda_r / dT9 */
+/* cell c and weight w in [0, 1] of value v on increasing nodes x[0..m), clamped */
+static void grid_cell(const double* x, int m, double v, int* c, double* w) {
+    if (v <= x[0]) { *c = 0; *w = 0.0; return; }
+    if (v >= x[m - 1]) { *c = m - 2; *w = 1.0; return; }
+    int i = 0;
+    while (v > x[i + 1]) ++i;
+    *c = i;
+    *w = (v - x[i]) / (x[i + 1] - x[i]);
+}
+
+/* ln lambda of table tb at (log10(rho Ye), T9) by bilinear interpolation, and
+   its T9-derivative (0 outside the temperature range) */
+static double table_lnl(const ora_network* net, int tb, double lrye, double T9, double* dl) {
+    int i, j;
+    double u, v;
+    grid_cell(net->tab_dens, net->tab_nd, lrye, &i, &u);
+    grid_cell(net->tab_t9, net->tab_nt, T9, &j, &v);
+    const double* L = net->tab_lnl + (size_t)tb * net->tab_nd * net->tab_nt;
+    const int nt = net->tab_nt;
+    double l00 = L[i * nt + j], l01 = L[i * nt + j + 1];
+    double l10 = L[(i + 1) * nt + j], l11 = L[(i + 1) * nt + j + 1];
+    double at_j = (1 - u) * l00 + u * l10;      /* along density, at T node j */
+    double at_j1 = (1 - u) * l01 + u * l11;     /* and at node j+1 */
+    int inside = T9 > net->tab_t9[0] && T9 < net->tab_t9[nt - 1];
+    *dl = inside ? (at_j1 - at_j) / (net->tab_t9[j + 1] - net->tab_t9[j]) : 0.0;
+    return (1 - v) * at_j + v * at_j1;
+}
+
 void ora_rate_factors(const ora_network* net, double T9, double rho, double zeta,
-                      const double* ln_mult, double* k, double* g) {
+                      double ye, const double* ln_mult, double* k, double* g) {
     double t13 = cbrt(T9);
     double phi[7] = {1.0, 1.0 / T9, 1.0 / t13, t13, T9, T9 * t13 * t13, log(T9)};
     double dphi[7] = {0.0,
@@ -156,6 +195,12 @@ void ora_rate_factors(const ora_network* net, double T9, double rho, double zeta
         double p = ln_mult ? ln_mult[r] : 0.0;
         double rp = 1.0;
         for (int m = 1; m < n_reactants(net, r); ++m) rp *= rho;
+        if (net->tab_of && net->tab_of[r] >= 0) {
+            /* a tabulated rate replaces the fit's exponent */
+            double dl;
+            e = table_lnl(net, net->tab_of[r], log10(rho * ye), T9, &dl);
+            de = dl;
+        }
         /* screening: H_r = s_r sqrt(rho zeta) T6^(-3/2), dH/dT9 = -1.5 H / T9 */
         double H = 0.0;
         if (net->screen && zeta > 0.0)
@@ -325,11 +370,11 @@ static int state_dim(const ora_network* net) { return net->N + (net->self_heatin
 /* Public single-state evaluations (used by the tests).  T9 is the fixed
    temperature when the network has no self-heating; otherwise x[N] is used. */
 void ora_rhs(const ora_network* net, const double* x, double T9, double rho, double zeta,
-             const double* ln_mult, double* f, double* edot) {
+             double ye, const double* ln_mult, double* f, double* edot) {
     double* k = malloc(sizeof(double) * (net->R + 1));
     double* Rr = malloc(sizeof(double) * (net->R + 1));
     rxn_species* L = species_lists(net);
-    ora_rate_factors(net, net->self_heating ? x[net->N] : T9, rho, zeta, ln_mult, k, NULL);
+    ora_rate_factors(net, net->self_heating ? x[net->N] : T9, rho, zeta, ye, ln_mult, k, NULL);
     rhs_given_k(net, L, x, k, f, edot, Rr);
     free(L);
     free(k);
@@ -337,12 +382,12 @@ void ora_rhs(const ora_network* net, const double* x, double T9, double rho, dou
 }
 
 void ora_jacobian(const ora_network* net, const double* x, double T9, double rho,
-                  double zeta, const double* ln_mult, double* J) {
+                  double zeta, double ye, const double* ln_mult, double* J) {
     double* k = malloc(sizeof(double) * (net->R + 1));
     double* g = malloc(sizeof(double) * (net->R + 1));
     double* Rr = malloc(sizeof(double) * (net->R + 1));
     rxn_species* L = species_lists(net);
-    ora_rate_factors(net, net->self_heating ? x[net->N] : T9, rho, zeta, ln_mult, k, g);
+    ora_rate_factors(net, net->self_heating ? x[net->N] : T9, rho, zeta, ye, ln_mult, k, g);
     jacobian_given_k(net, L, x, k, g, J, Rr);
     free(L);
     free(k);
@@ -499,14 +544,22 @@ typedef struct {
     double rho, T9_fixed;
     const double* ln_mult;
     int32_t* cnt;
-    double zeta;
+    double zeta, ye;
 } zone_ctx;
+
+/* Ye = sum Z_i Y_i of a composition (1 without charges) */
+static double electron_fraction(const ora_network* net, const double* Y) {
+    if (!net->charge) return 1.0;
+    double ye = 0.0;
+    for (int i = 0; i < net->N; ++i) ye += net->charge[i] * Y[i];
+    return ye;
+}
 
 /* rate factors for state x (fixed temperature or x[N]) */
 static void rates_for(zone_ctx* z, const double* x, work_t* W, int with_g) {
     const ora_network* net = z->net;
     double T9 = net->self_heating ? x[net->N] : z->T9_fixed;
-    ora_rate_factors(net, T9, z->rho, z->zeta, z->ln_mult, W->k, with_g ? W->g : NULL);
+    ora_rate_factors(net, T9, z->rho, z->zeta, z->ye, z->ln_mult, W->k, with_g ? W->g : NULL);
     z->cnt[C_TEVAL]++;
 }
 
@@ -546,7 +599,7 @@ static int burn_zone(const ora_network* net, const ora_options* opt,
     const int has_E = net->Q != NULL;
     const double t_end = opt->t_end, rtol = opt->rtol, atol = opt->atol;
     const int kmax = opt->max_order > 0 && opt->max_order < KMAX ? opt->max_order : KMAX;
-    zone_ctx z = {net, rho, T9_0, ln_mult, cnt, zeta};
+    zone_ctx z = {net, rho, T9_0, ln_mult, cnt, zeta, electron_fraction(net, Y0)};
     double* f0 = malloc(sizeof(double) * n);   /* f(x_0), for the first predictor */
     memset(cnt, 0, sizeof(int32_t) * C_COUNT);
 
@@ -840,7 +893,7 @@ int ora_replay(const ora_network* net, const ora_options* opt, const double* Y0,
     const int N = net->N, n = state_dim(net);
     work_t* W = work_alloc(net);
     int32_t cnt[C_COUNT] = {0};
-    zone_ctx z = {net, rho, T9_0, ln_mult, cnt, zeta};
+    zone_ctx z = {net, rho, T9_0, ln_mult, cnt, zeta, electron_fraction(net, Y0)};
     int nh = 0, rc = 0;
     for (int i = 0; i < N; ++i) W->x1[i] = Y0[i];
     if (net->self_heating) W->x1[N] = T9_0;
@@ -910,7 +963,7 @@ int ora_forward_sensitivity(const ora_network* net, double T9_fixed, double rho,
     const int P = R + n + (net->self_heating ? 0 : 1);
     work_t* W = work_alloc(net);
     int32_t cnt[C_COUNT] = {0};
-    zone_ctx z = {net, rho, T9_fixed, ln_mult, cnt, zeta};
+    zone_ctx z = {net, rho, T9_fixed, ln_mult, cnt, zeta, electron_fraction(net, tape_x)};
     /* history of sensitivity matrices, newest first */
     double* Sh = calloc((size_t)HMAX * n * P, sizeof(double));
     double* SEh = calloc((size_t)HMAX * P, sizeof(double));

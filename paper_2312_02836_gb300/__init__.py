@@ -49,11 +49,21 @@ def _topology(spec):
                   scale=_np(getattr(spec, "scale", None), np.float64),
                   ap_pg=_np(getattr(spec, "ap_pg", None), np.int8),
                   ap_coeffs=_np(getattr(spec, "ap_coeffs", None), np.float64),
-                  screen=_np(getattr(spec, "screen", None), np.float64))
+                  screen=_np(getattr(spec, "screen", None), np.float64),
+                  tab_of=_np(getattr(spec, "tab_of", None), np.int32),
+                  tab_dens=_np(getattr(spec, "tab_dens", None), np.float64),
+                  tab_t9=_np(getattr(spec, "tab_t9", None), np.float64),
+                  tab_lnl=_np(getattr(spec, "tab_lnl", None), np.float64),
+                  charge=_np(getattr(spec, "charge", None), np.float64))
     p = lambda a: None if a is None else a.ctypes.data
     topo = _abi.Topology(int(spec.N), int(spec.R), p(arrays["reac"]), p(arrays["prod"]),
                          p(arrays["Q"]), p(arrays["scale"]), int(bool(spec.self_heating)),
-                         p(arrays["ap_pg"]), p(arrays["ap_coeffs"]), p(arrays["screen"]))
+                         p(arrays["ap_pg"]), p(arrays["ap_coeffs"]), p(arrays["screen"]),
+                         p(arrays["tab_of"]),
+                         0 if arrays["tab_dens"] is None else arrays["tab_dens"].size,
+                         0 if arrays["tab_t9"] is None else arrays["tab_t9"].size,
+                         p(arrays["tab_dens"]), p(arrays["tab_t9"]), p(arrays["tab_lnl"]),
+                         p(arrays["charge"]))
     return arrays, topo, p(arrays["coef"])
 
 

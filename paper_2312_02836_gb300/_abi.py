@@ -35,7 +35,10 @@ class Topology(C.Structure):
                 ("reactants", C.c_void_p), ("products", C.c_void_p),
                 ("Q", C.c_void_p), ("scale", C.c_void_p),
                 ("self_heating", C.c_int32), ("ap_pg", C.c_void_p),
-                ("ap_coeffs", C.c_void_p), ("screen", C.c_void_p)]
+                ("ap_coeffs", C.c_void_p), ("screen", C.c_void_p),
+                ("tab_of", C.c_void_p), ("tab_nd", C.c_int32), ("tab_nt", C.c_int32),
+                ("tab_dens", C.c_void_p), ("tab_t9", C.c_void_p),
+                ("tab_lnl", C.c_void_p), ("charge", C.c_void_p)]
 
 
 class NetInfo(C.Structure):

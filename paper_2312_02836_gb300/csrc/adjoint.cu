@@ -102,6 +102,7 @@ __device__ bool adj_init(const Net& t, AdjZone& Zs, const WS& w, const AWS& a,
   s.rho2 = s.rho * s.rho;
   s.T9f = A.tape.T9f[z];
   s.scr = A.tape.scr[z];
+  tab_zone(t, s, rec_ptr(t, A, z, 0) + 2);   // the recorded initial state
   s.lnm = A.lnm ? (A.lnm_per_zone ? A.lnm + (size_t)z * t.R : A.lnm) : nullptr;
   if (!t.sh) eval_rates(t, s, w, t_powers(s.T9f, true, s.scr), s.T9f, true);
   return S == 0;

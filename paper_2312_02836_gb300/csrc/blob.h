@@ -87,6 +87,14 @@ struct BlobHeader {
   int32_t n_ap;         // effective (alpha,p)(p,gamma) rates
   int32_t o_scr;        // double [R] weak-screening strengths s_r
   int32_t has_scr;      // 1 when the network is screened
+  int32_t n_tab;        // tables of tabulated rates (0: none)
+  int32_t tab_nd, tab_nt;  // their grid: density and temperature nodes
+  int32_t o_tab_of;     // int32 [R] table of reaction r, -1 = fit
+  int32_t o_tab_dens;   // double [tab_nd] log10(rho Ye) nodes
+  int32_t o_tab_t9;     // double [tab_nt] T9 nodes
+  int32_t o_tab_lnl;    // double [n_tab * tab_nd * tab_nt] ln lambda at the nodes
+  int32_t o_charge;     // double [N] species charges
+  int32_t pad2_;
 };
 
 }  // namespace nb

@@ -153,6 +153,31 @@ std::string specialized_source(const std::vector<uint8_t>& blob, int variant) {
   else o("  LV k;\n");
   o("  LV f0, xh, eh, th;\n};\n\n");
 
+  // ---- rate tables (grid, ln lambda at the nodes, charges) as literal arrays
+  const bool has_tab = h.n_tab > 0;
+  const int32_t* tab_of = arr<int32_t>(blob, h.o_tab_of);
+  auto lit_array = [&](const char* name, const double* v, size_t cnt) {
+    o("__device__ const double %s[%zu] = {", name, cnt);
+    for (size_t i = 0; i < cnt; ++i) o("%s%s", i ? ", " : "", lit(v[i]).c_str());
+    o("};\n");
+  };
+  if (has_tab) {
+    lit_array("NB_TAB_T9", arr<double>(blob, h.o_tab_t9), (size_t)h.tab_nt);
+    lit_array("NB_TAB_DENS", arr<double>(blob, h.o_tab_dens), (size_t)h.tab_nd);
+    lit_array("NB_TAB_L", arr<double>(blob, h.o_tab_lnl),
+              (size_t)h.n_tab * h.tab_nd * h.tab_nt);
+    o("\n");
+  }
+  o("template <class V>\nNB_HD __forceinline__ void tab_zone(const GNet&, Zone& s, const V& x0) {\n"
+    "  s.tab_i = 0;\n  s.tab_u = 0.0;\n");
+  if (has_tab) {
+    const double* charge = arr<double>(blob, h.o_charge);
+    o("  double ye = 0.0;\n");
+    for (int i = 0; i < N; ++i) o("  ye = fma(%s, x0[%d], ye);\n", lit(charge[i]).c_str(), i);
+    o("  density_cell(NB_TAB_DENS, %d, s.rho, ye, s);\n", h.tab_nd);
+  }
+  o("}\n\n");
+
   // ---- rates
   const int32_t* ap = arr<int32_t>(blob, h.o_ap);
   const double* apc = arr<double>(blob, h.o_apc);
@@ -174,12 +199,21 @@ std::string specialized_source(const std::vector<uint8_t>& blob, int variant) {
   auto emit_full = [&](int r, const char* ind, bool g) {
     const double* a = coef + 7 * r;
     const char* rp = nrho[r] == 0 ? "1.0" : (nrho[r] == 1 ? "s.rho" : "s.rho2");
-    o("%se = rate_exponent(%s, p, T9);\n", ind, fit7(a, 0).c_str());
+    const int tb = has_tab ? tab_of[r] : -1;
+    if (tb >= 0)
+      o("%se = table_lnl(NB_TAB_L + %lld, %d, s, tc, &dl);\n", ind,
+        (long long)tb * h.tab_nd * h.tab_nt, h.tab_nt);
+    else
+      o("%se = rate_exponent(%s, p, T9);\n", ind, fit7(a, 0).c_str());
     o("%sif (lnm) e += lnm[%d];\n", ind, r);
     if (has_scr) o("%se = %se);\n", ind, scr_e(r).c_str());
     if (ap[r] < 0) {
       o("%sw.k[%d] = exp_tang(e) * (%s * %s);\n", ind, r, rp, lit(scale[r]).c_str());
-      if (g) o("%sif (with_g) w.g[%d] = %s;\n", ind, r, dlog(r, a).c_str());
+      if (g) {
+        const std::string gd = tb >= 0 ? (has_scr ? "fma(" + lit(scr[r]) + ", p.hzd, dl)" : "dl")
+                                       : dlog(r, a);
+        o("%sif (with_g) w.g[%d] = %s;\n", ind, r, gd.c_str());
+      }
       return;
     }
     const double* b = apc + 21 * ap[r];
@@ -198,6 +232,7 @@ std::string specialized_source(const std::vector<uint8_t>& blob, int variant) {
   };
   o("NB_HD __forceinline__ void eval_rates(const GNet&, const Zone& s, GWS& w, const TPow& p,"
     " double T9, bool with_g) {\n  const double* lnm = s.lnm;\n  double e;\n");
+  if (has_tab) o("  const TCell tc = t_cell(NB_TAB_T9, %d, T9);\n  double dl;\n", h.tab_nt);
   for (int r = 0; r < R; ++r) emit_full(r, "  ", sh);
   o("}\n\n");
 
@@ -212,8 +247,9 @@ std::string specialized_source(const std::vector<uint8_t>& blob, int variant) {
   if (sh) {
     o("  const TPow p = t_powers(T9, false, s.scr);\n  const DPhi d = delta_phi(p, ref, T9, T9ref);\n"
       "  const double* lnm = s.lnm;\n  double de, e;\n");
+    if (has_tab) o("  const TCell tc = t_cell(NB_TAB_T9, %d, T9);\n  double dl;\n", h.tab_nt);
     for (int r = 0; r < R; ++r) {
-      if (ap[r] >= 0) {
+      if (ap[r] >= 0 || (has_tab && tab_of[r] >= 0)) {
         emit_full(r, "  ", false);
         continue;
       }

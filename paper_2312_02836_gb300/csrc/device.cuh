@@ -32,6 +32,9 @@ struct Net {
   double inv_n;
   const double *coef, *Q, *scale, *rhs_c, *dt_m, *js_c, *rg_c, *apc;
   const double* scr;   // weak-screening strengths s_r, null without screening
+  const int32_t* tab_of;   // table of reaction r (-1 fit), null without tables
+  const double *tab_dens, *tab_t9, *tab_lnl, *charge;
+  int tab_nd, tab_nt;
   const int32_t *nrho, *nreac, *rhs_ptr, *js_ptr, *diag_orig, *rg_ptr, *ap;
   const int16_t *reac, *rhs_r, *dt_r, *dt_o, *dt_j, *js_src, *lslot, *uslot, *dslot;
   const int16_t *fw_s, *fw_c, *bw_s, *bw_c, *tfw_s, *tfw_c, *tbw_s, *tbw_c, *rg_i;
@@ -59,6 +62,10 @@ NB_HD inline Net make_net(const unsigned char* b) {
   t.rg_c = at<double>(b, h->o_rg_c);
   t.apc = at<double>(b, h->o_apc); t.ap = at<int32_t>(b, h->o_ap);
   t.scr = h->has_scr ? at<double>(b, h->o_scr) : nullptr;
+  t.tab_of = h->n_tab > 0 ? at<int32_t>(b, h->o_tab_of) : nullptr;
+  t.tab_dens = at<double>(b, h->o_tab_dens); t.tab_t9 = at<double>(b, h->o_tab_t9);
+  t.tab_lnl = at<double>(b, h->o_tab_lnl); t.charge = at<double>(b, h->o_charge);
+  t.tab_nd = h->tab_nd; t.tab_nt = h->tab_nt;
   t.nrho = at<int32_t>(b, h->o_nrho); t.nreac = at<int32_t>(b, h->o_nreac);
   t.rhs_ptr = at<int32_t>(b, h->o_rhs_ptr); t.js_ptr = at<int32_t>(b, h->o_js_ptr);
   t.diag_orig = at<int32_t>(b, h->o_diag_orig); t.rg_ptr = at<int32_t>(b, h->o_rg_ptr);
@@ -139,10 +146,15 @@ NB_HD __forceinline__ WS make_ws(const Net& t, double* lane_base) {
 // ---------------------------------------------------------------- model
 
 // k_r of reaction r (and g_r = d ln lambda_r / dT9 when g) at T9 with powers p
+// (tc: the temperature cell of the rate tables at T9)
 NB_HD __forceinline__ double rate_full(const Net& t, const Zone& s, int r, const TPow& p,
-                                       double T9, double* g) {
+                                       double T9, const TCell& tc, double* g) {
   const double* a = t.coef + 7 * r;
-  double e = rate_exponent(a[0], a[1], a[2], a[3], a[4], a[5], a[6], p, T9);
+  const int tb = t.tab_of ? t.tab_of[r] : -1;
+  double dl = 0.0;
+  double e = tb >= 0 ? table_lnl(t.tab_lnl + (size_t)tb * t.tab_nd * t.tab_nt, t.tab_nt, s,
+                                 tc, &dl)
+                     : rate_exponent(a[0], a[1], a[2], a[3], a[4], a[5], a[6], p, T9);
   if (s.lnm) e += s.lnm[r];
   const double sr = t.scr ? t.scr[r] : 0.0;
   if (t.scr) e = fma(sr, p.hz, e);
@@ -151,7 +163,7 @@ NB_HD __forceinline__ double rate_full(const Net& t, const Zone& s, int r, const
   const int api = t.ap[r];
   if (api < 0) {
     if (g) {
-      *g = rate_dlog(a[1], a[2], a[3], a[4], a[5], a[6], p);
+      *g = tb >= 0 ? dl : rate_dlog(a[1], a[2], a[3], a[4], a[5], a[6], p);
       if (t.scr) *g = fma(sr, p.hzd, *g);
     }
     return exp_tang(e) * (rp * t.scale[r]);
@@ -183,10 +195,11 @@ NB_HD inline void eval_rates(const Net& t, const Zone& s, const WS& w, const TPo
                              double T9, bool with_g) {
   // one warp per scheduler leaves FP64 latency exposed: two reactions per
   // iteration and two partial sums per exponent give independent chains
+  const TCell tc = t.tab_of ? t_cell(t.tab_t9, t.tab_nt, T9) : TCell{0, 0.0, 1.0, false};
 #pragma unroll 2
   for (int r = 0; r < t.R; ++r) {
     double g;
-    w.k[r] = rate_full(t, s, r, p, T9, with_g ? &g : nullptr);
+    w.k[r] = rate_full(t, s, r, p, T9, tc, with_g ? &g : nullptr);
     if (with_g) w.g[r] = g;
   }
 }
@@ -198,14 +211,29 @@ NB_HD inline void eval_rates_near(const Net& t, const Zone& s, const WS& w, doub
                                   const TPow& ref, double T9ref) {
   const TPow p = t_powers(T9, false, s.scr);
   const DPhi d = delta_phi(p, ref, T9, T9ref);
+  const TCell tc = t.tab_of ? t_cell(t.tab_t9, t.tab_nt, T9) : TCell{0, 0.0, 1.0, false};
 #pragma unroll 2
   for (int r = 0; r < t.R; ++r) {
     const double* a = t.coef + 7 * r;
     double de = rate_delta(a[1], a[2], a[3], a[4], a[5], a[6], d);
     if (t.scr) de = fma(t.scr[r], d.d7, de);
-    if (t.ap[r] < 0 && small_delta(de)) w.k[r] = rate_near(w.kp[r], de);
-    else w.k[r] = rate_full(t, s, r, p, T9, nullptr);
+    // tabulated and effective rates always take the full evaluation
+    if (t.ap[r] < 0 && !(t.tab_of && t.tab_of[r] >= 0) && small_delta(de))
+      w.k[r] = rate_near(w.kp[r], de);
+    else
+      w.k[r] = rate_full(t, s, r, p, T9, tc, nullptr);
   }
+}
+
+// the zone's density cell of the rate tables: Ye = sum Z_i Y_i of x0
+template <class V>
+NB_HD __forceinline__ void tab_zone(const Net& t, Zone& s, const V& x0) {
+  s.tab_i = 0;
+  s.tab_u = 0.0;
+  if (!t.tab_of) return;
+  double ye = 0.0;
+  for (int i = 0; i < t.N; ++i) ye = fma(t.charge[i], x0[i], ye);
+  density_cell(t.tab_dens, t.tab_nd, s.rho, ye, s);
 }
 
 NB_HD __forceinline__ void save_ref_rates(const Net& t, const WS& w) {

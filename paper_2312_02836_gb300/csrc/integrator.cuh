@@ -12,6 +12,8 @@
 //   eval_rates(t, s, w, p, T9, with_g)  k_r (and g_r = d ln lambda_r/dT9),
 //                                     p = t_powers(T9, with_g)
 //   save_ref_rates(t, w)              kp_r = k_r (the reference rates)
+//   tab_zone(t, s, x0)                the zone's density cell of the rate
+//                                     tables, from its initial composition
 //   eval_rates_near(t, s, w, T9, ref, T9ref)  k_r from kp_r (rate_near)
 //   eval_terms(t, w, v)               rr_r = k_r prod Y of the reactants
 //   eval_f(t, w, v, out)              out = f(v) from rr
@@ -94,6 +96,8 @@ struct Zone {
   long long z;
   double t, h, E, T9f, rho, rho2, tend;
   double scr;                 // sqrt(rho zeta) 10^-4.5: H_r = s_r scr T9^(-3/2)
+  int tab_i;                  // density cell of the rate tables (log10 rho Ye)
+  double tab_u;               // and the weight within it
   const double* lnm;
   int k, nh, hh, nconsec, nfail, status;
   int c_acc, c_rej_err, c_rej_newton, c_newton, c_jac, c_rhs, c_teval, c_edot;
@@ -181,6 +185,52 @@ NB_HD __forceinline__ double rate_dlog(double a1, double a2, double a3, double a
   g2 = fma(a6, p.iT, g2);
   g1 = fma(a3, p.d3, g1);
   return g1 + g2;
+}
+
+// Tabulated rates: ln lambda bilinear in (log10 rho Ye, T9) on a rectilinear
+// grid, clamped to its edges.  The density cell is the zone's (Ye from its
+// initial composition, held over the burn); the temperature cell is found
+// once per rate evaluation.
+
+// cell c and weight w in [0, 1] of v on increasing nodes x[0..m), clamped
+NB_HD __forceinline__ void grid_cell(const double* x, int m, double v, int& c, double& w) {
+  if (!(v > x[0])) { c = 0; w = 0.0; return; }
+  if (v >= x[m - 1]) { c = m - 2; w = 1.0; return; }
+  int i = 0;
+  while (v > x[i + 1]) ++i;       // stops at i <= m - 2, since v < x[m-1]
+  c = i;
+  w = (v - x[i]) / (x[i + 1] - x[i]);
+}
+
+struct TCell {
+  int j;             // temperature cell
+  double v, dt;      // weight within it, its width
+  bool inside;       // strictly inside the grid (else the T9 slope is 0)
+};
+
+NB_HD __forceinline__ TCell t_cell(const double* t9, int nt, double T9) {
+  TCell c;
+  grid_cell(t9, nt, T9, c.j, c.v);
+  c.dt = t9[c.j + 1] - t9[c.j];
+  c.inside = T9 > t9[0] && T9 < t9[nt - 1];
+  return c;
+}
+
+// the zone's density cell from Ye = sum Z_i Y_i (accumulated by the caller)
+NB_HD __forceinline__ void density_cell(const double* dens, int nd, double rho, double ye,
+                                        Zone& s) {
+  grid_cell(dens, nd, log10(rho * ye), s.tab_i, s.tab_u);
+}
+
+// ln lambda of one table L [nd, nt] and its T9-derivative
+NB_HD __forceinline__ double table_lnl(const double* L, int nt, const Zone& s, const TCell& c,
+                                       double* dl) {
+  const int a = s.tab_i * nt + c.j, b = a + nt;
+  const double u = s.tab_u;
+  const double at_j = (1.0 - u) * L[a] + u * L[b];
+  const double at_j1 = (1.0 - u) * L[a + 1] + u * L[b + 1];
+  *dl = c.inside ? (at_j1 - at_j) / c.dt : 0.0;
+  return (1.0 - c.v) * at_j + c.v * at_j1;
 }
 
 // Effective (alpha,p)(p,gamma) rate from the exponents of its four channels
@@ -478,6 +528,7 @@ NB_HD __forceinline__ bool zone_init(const NT& t, Zone& s, WT& w, const BurnPara
     fin = fin && finite_bits(y);
   }
   if (t.sh) x0[N] = s.T9f;
+  tab_zone(t, s, x0);
   w.th[0] = 0.0;
   w.eh[0] = 0.0;
   if (P.use_tape) {

@@ -290,6 +290,37 @@ int build_blob(const nb_topology* T, const double* coeffs,
     }
   }
   const int n_ap = (int)(apc.size() / 21);
+  // tabulated rates: validate and copy the grid, the tables and the charges
+  std::vector<int32_t> tab_of(R > 0 ? R : 1, -1);
+  std::vector<double> tab_dens(1, 0.0), tab_t9(1, 0.0), tab_lnl(1, 0.0), charge(1, 0.0);
+  int n_tab = 0, n_tabr = 0;
+  if (T->tab_of) {
+    const int nd = T->tab_nd, nt = T->tab_nt;
+    if (nd < 2 || nt < 2 || nd > 4096 || nt > 4096 || !T->tab_dens || !T->tab_t9 ||
+        !T->tab_lnl || !T->charge)
+      return NB_E_ARG;
+    for (int r = 0; r < R; ++r) {
+      const int tb = T->tab_of[r];
+      if (tb < -1) return NB_E_ARG;
+      if (tb >= 0 && T->ap_pg && T->ap_pg[r]) return NB_E_ARG;   // tabulated or effective
+      n_tab = std::max(n_tab, tb + 1);
+      n_tabr += tb >= 0;
+      tab_of[r] = tb;
+    }
+    tab_dens.assign(T->tab_dens, T->tab_dens + nd);
+    tab_t9.assign(T->tab_t9, T->tab_t9 + nt);
+    for (int a = 0; a + 1 < nd; ++a)
+      if (!(tab_dens[a + 1] > tab_dens[a])) return NB_E_ARG;
+    for (int a = 0; a + 1 < nt; ++a)
+      if (!(tab_t9[a + 1] > tab_t9[a])) return NB_E_ARG;
+    for (double v : tab_dens) if (!std::isfinite(v)) return NB_E_ARG;
+    for (double v : tab_t9) if (!std::isfinite(v)) return NB_E_ARG;
+    tab_lnl.assign(T->tab_lnl, T->tab_lnl + (size_t)std::max(n_tab, 1) * nd * nt);
+    if (n_tab == 0) tab_lnl.assign(1, 0.0);
+    for (double v : tab_lnl) if (!std::isfinite(v)) return NB_E_ARG;
+    charge.assign(T->charge, T->charge + N);
+    for (double v : charge) if (!std::isfinite(v)) return NB_E_ARG;
+  }
   std::vector<double> scr(R > 0 ? R : 1, 0.0);
   if (T->screen)
     for (int r = 0; r < R; ++r) {
@@ -315,6 +346,14 @@ int build_blob(const nb_topology* T, const double* coeffs,
   h.n_ap = n_ap;
   h.o_scr = B.add(scr);
   h.has_scr = T->screen ? 1 : 0;
+  h.n_tab = n_tab;
+  h.tab_nd = T->tab_of ? T->tab_nd : 0;
+  h.tab_nt = T->tab_of ? T->tab_nt : 0;
+  h.o_tab_of = B.add(tab_of);
+  h.o_tab_dens = B.add(tab_dens);
+  h.o_tab_t9 = B.add(tab_t9);
+  h.o_tab_lnl = B.add(tab_lnl);
+  h.o_charge = B.add(charge);
   h.o_Q = B.add(Q);
   h.o_scale = B.add(scale);
   h.o_nrho = B.add(nrho);
@@ -381,7 +420,7 @@ int build_blob(const nb_topology* T, const double* coeffs,
   }
   // powers of T9, 7-term exponents, k_r; an effective rate adds three
   // exponents and their combination
-  h.fl_teval = 2 + 14 * (int64_t)R + 45 * (int64_t)n_ap +
+  h.fl_teval = 2 + 14 * (int64_t)(R - n_tabr) + 10 * (int64_t)n_tabr + 45 * (int64_t)n_ap +
                (T->screen ? 3 + 2 * (int64_t)(R + n_ap) : 0);
   h.fl_teval_g = 6 + 10 * (int64_t)R + 38 * (int64_t)n_ap;  // d ln lambda / dT9
   h.fl_terms = terms;                        // R_r = k_r prod Y

@@ -4,6 +4,7 @@ checked against the generic kernel, bit for bit, by the GPU tests."""
 import ctypes as C
 import re
 
+import numpy as np
 import pytest
 
 import gen
@@ -106,6 +107,28 @@ def test_screening_in_the_source():
     spec = gen.network("chain13_heat_scr")
     spec.screen = spec.screen.copy()
     spec.screen[2] = -1.0
+    arrays, topo, coef = nb._topology(spec)
+    n = C.c_int64()
+    assert _abi.load().nb_specialize_source(C.byref(topo), coef, 0, None, 0,
+                                            C.byref(n)) == -1
+
+
+def test_tables_in_the_source():
+    # the tables are literal device arrays; every tabulated rate reads its
+    # table in the full evaluation and takes it (not the near update) in the
+    # near evaluation; the zone's Ye comes from the literal charges
+    net = gen.network("chain13_heat_tab")
+    n_tab = int((net.tab_of >= 0).sum())
+    src = nb.specialized_source(net, 0)
+    assert "__device__ const double NB_TAB_L[%d]" % net.tab_lnl.size in src
+    assert src.count("e = table_lnl(NB_TAB_L + ") == 2 * n_tab
+    assert src.count("rate_near(w.kp[") == net.R - n_tab
+    assert src.count("ye = fma(") == net.N
+    # tabulated and effective at once: rejected on the host
+    spec = gen.network("chain13_heat_tab")
+    spec.ap_pg = np.zeros(spec.R, dtype=np.int8)
+    spec.ap_pg[2] = 1
+    spec.ap_coeffs = np.zeros((spec.R, 3, 7))
     arrays, topo, coef = nb._topology(spec)
     n = C.c_int64()
     assert _abi.load().nb_specialize_source(C.byref(topo), coef, 0, None, 0,

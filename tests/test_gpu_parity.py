@@ -8,7 +8,7 @@ import pytest
 
 import gen
 import oracle
-from tests.parity import compare, to_numpy
+from tests.parity import TABULATED, compare, to_numpy
 
 pytestmark = pytest.mark.gpu
 
@@ -50,7 +50,7 @@ def gpu_run(nb, torch, net_c, z, s, **kw):
 
 
 CASES = [("chain13", 4096), ("chain13_literal", 1024), ("chain13_heat", 2048),
-         ("chain13_heat_ap", 2048), ("chain13_heat_scr", 2048),
+         ("chain13_heat_ap", 2048), ("chain13_heat_scr", 2048), ("chain13_heat_tab", 2048),
          ("net48", 256), ("net48_adjoint", 128), ("net128_heat", 16)]
 
 
@@ -79,7 +79,8 @@ def test_parity_with_oracle(name, Z, kernel):
         assert keep.sum() >= Z - 3
         g = {k: v[keep] for k, v in g.items()}
         o = {k: o[k][keep] for k in ("Y", "T9", "E", "counters", "status")}
-    rep = compare(g, o, s["atol"])
+    bar = TABULATED if getattr(net, "tab_of", None) is not None else {}
+    rep = compare(g, o, s["atol"], rtol=s["rtol"], **bar)
     if name != "chain13_literal":
         mass = (g["Y"] * net.A).sum(1)
         assert np.abs(mass - 1.0).max() <= 1e-12

@@ -29,7 +29,7 @@ def _equal(a, b):
 
 
 CASES = [("chain13", 2048), ("chain13_literal", 1024), ("chain13_heat", 2048),
-         ("chain13_heat_ap", 1024), ("chain13_heat_scr", 1024)]
+         ("chain13_heat_ap", 1024), ("chain13_heat_scr", 1024), ("chain13_heat_tab", 1024)]
 
 
 @pytest.mark.parametrize("variant", [1, 2, 3])

@@ -75,6 +75,69 @@ def test_rate_temperature_derivative_fd():
         np.testing.assert_allclose(g, fd, rtol=1e-6, atol=1e-8 * np.abs(g).max())
 
 
+# ---------------------------------------------------------------- tabulated rates
+
+def _tab_net(fn, reac=((0,),), prod=((1,),), N=2, charge=(1.0, 1.0)):
+    """One tabulated reaction whose table holds fn(log10 rho Ye, T9) at the
+    nodes of the generator's grid."""
+    net = make_net(list(reac), list(prod), N=N, lam=[1.0])
+    D, T = gen.workloads.TAB_DENS, gen.workloads.TAB_T9
+    net.tab_of = np.zeros(1, dtype=np.int32)
+    net.tab_dens, net.tab_t9 = D.copy(), T.copy()
+    net.tab_lnl = fn(D[:, None], T[None, :])[None, :, :].copy()
+    net.charge = np.asarray(charge, dtype=np.float64)
+    return net
+
+
+def test_table_bilinear_exact_nodes_derivative_and_clamp():
+    # ln lambda = a + b x + c T + d x T is bilinear, so interpolation is exact
+    # anywhere in the grid, and d ln lambda / dT9 = c + d x
+    a, b, c, d = 1.5, 0.7, -0.4, 0.05
+    net = _tab_net(lambda x, T: a + b * x + c * T + d * x * T)
+    for T9, rho, ye in ((0.85, 3e5, 0.5), (3.3, 7e6, 0.45), (1.0, 1e6, 1.0), (9.1, 2e7, 0.3)):
+        x = math.log10(rho * ye)
+        k, g = oracle.rate_factors(net, T9, rho, ye=ye)
+        np.testing.assert_allclose(k, [math.exp(a + b * x + c * T9 + d * x * T9)], rtol=1e-13)
+        np.testing.assert_allclose(g, [c + d * x], rtol=1e-12)
+    # beyond the grid: the edge value, no temperature slope
+    k, g = oracle.rate_factors(net, 12.0, 1e6, ye=1.0)
+    np.testing.assert_allclose(k, [math.exp(a + b * 6.0 + c * 10.0 + d * 60.0)], rtol=1e-13)
+    assert g[0] == 0.0
+    k, _ = oracle.rate_factors(net, 2.0, 1e9, ye=1.0)          # log10(rho Ye) = 9 > 8
+    np.testing.assert_allclose(k, [math.exp(a + b * 8.0 + c * 2.0 + d * 16.0)], rtol=1e-13)
+
+
+def test_table_read_equals_scipy_grid_interpolator():
+    # the generated tables of the tabulated workload, read by the oracle and
+    # by SciPy's linear RegularGridInterpolator (an independent routine)
+    from scipy.interpolate import RegularGridInterpolator
+    net = gen.network("chain13_heat_tab")
+    rng = np.random.default_rng(11)
+    for _ in range(20):
+        T9 = rng.uniform(0.3, 10.0)
+        rho, ye = 10 ** rng.uniform(4.3, 8.3), 0.5
+        k, _ = oracle.rate_factors(net, T9, rho, ye=ye)
+        x = math.log10(rho * ye)
+        for r in np.nonzero(net.tab_of >= 0)[0]:
+            f = RegularGridInterpolator((net.tab_dens, net.tab_t9), net.tab_lnl[net.tab_of[r]])
+            n_r = int((net.reactants[r] >= 0).sum())
+            lnk = math.log(k[r] / rho ** (n_r - 1))
+            assert abs(lnk - f([[x, T9]])[0]) < 1e-12
+
+
+def test_table_reads_rho_ye_of_the_initial_composition():
+    # one-body decay 0 -> 1 whose table depends on density only: lambda =
+    # exp(-1 + 0.5 log10(rho Ye)) with Ye = sum Z_i Y_i = 3 * 0.1 + 1 * 0.2
+    net = _tab_net(lambda x, T: -1.0 + 0.5 * x + 0.0 * T, charge=(3.0, 1.0))
+    Y0 = np.array([[0.1, 0.2]])
+    rho, t_end = 4e6, 0.7
+    ye = 3.0 * 0.1 + 1.0 * 0.2
+    lam = math.exp(-1.0 + 0.5 * math.log10(rho * ye))
+    o = oracle.burn(net, Y0, np.array([2.0]), np.array([rho]), t_end, 1e-10, 1e-20)
+    assert o["status"][0] == 0
+    np.testing.assert_allclose(o["Y"][0, 0], 0.1 * math.exp(-lam * t_end), rtol=1e-7)
+
+
 # ---------------------------------------------------------------- screening
 
 def test_screening_factor_closed_form_and_zero_zeta():
