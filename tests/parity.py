@@ -32,8 +32,13 @@ import numpy as np
 # its weight w = atol + rtol |Y| (the error test), T9 and E to 1e-6
 # relative.  Measured over 2048 zones (host run of the device code against
 # the oracle): 0.16 of this bar at most, T9 4e-8, 0.6 % of zones on a
-# different step sequence.
-TABULATED = dict(same_rel=1e-6, same_w=1.0, scalar_rel=1e-6, max_diverged_frac=0.03)
+# different step sequence.  Near a kink the error test can accept or reject
+# a step on rounding, each flip shifting the step sequence; a zone crosses at
+# most the grid's 12 temperatures, so accepted-step counts may differ by up to
+# 12 (such zones are still held to the integration tolerance).  Measured on
+# the GPU: 3.
+TABULATED = dict(same_rel=1e-6, same_w=1.0, scalar_rel=1e-6, max_diverged_frac=0.03,
+                 max_step_diff=12)
 
 
 def compare(gpu: dict, ora: dict, atol: float, max_step_diff: int = 2,
