@@ -248,15 +248,37 @@ std::string specialized_source(const std::vector<uint8_t>& blob, int variant) {
     o("  const TPow p = t_powers(T9, false, s.scr);\n  const DPhi d = delta_phi(p, ref, T9, T9ref);\n"
       "  const double* lnm = s.lnm;\n  double de, e;\n");
     if (has_tab) o("  const TCell tc = t_cell(NB_TAB_T9, %d, T9);\n  double dl;\n", h.tab_nt);
+    // hot part: the small-delta updates, straight-line; a reaction whose
+    // delta is large is marked and evaluated in full in the cold part
+    // below, so the rarely run full evaluations do not sit between the hot
+    // instructions
+    o("  unsigned long long full = 0ull;\n");
+    int nbit = 0;
+    std::vector<int> marked;
     for (int r = 0; r < R; ++r) {
-      if (ap[r] >= 0 || (has_tab && tab_of[r] >= 0)) {
-        emit_full(r, "  ", false);
-        continue;
-      }
+      if (ap[r] >= 0 || (has_tab && tab_of[r] >= 0)) continue;
       o("  de = rate_delta(%s, d);\n", fit7(coef + 7 * r, 1).c_str());
       if (has_scr) o("  de = fma(%s, d.d7, de);\n", lit(scr[r]).c_str());
-      o("  if (small_delta(de)) {\n    w.k[%d] = rate_near(w.kp[%d], de);\n  } else {\n", r, r);
-      emit_full(r, "    ", false);
+      if (nbit < 64) {
+        o("  if (small_delta(de)) w.k[%d] = rate_near(w.kp[%d], de);\n"
+          "  else full |= 1ull << %d;\n", r, r, nbit);
+        marked.push_back(r);
+        ++nbit;
+      } else {
+        o("  if (small_delta(de)) {\n    w.k[%d] = rate_near(w.kp[%d], de);\n  } else {\n", r, r);
+        emit_full(r, "    ", false);
+        o("  }\n");
+      }
+    }
+    for (int r = 0; r < R; ++r)
+      if (ap[r] >= 0 || (has_tab && tab_of[r] >= 0)) emit_full(r, "  ", false);
+    if (!marked.empty()) {
+      o("  if (full) {\n");
+      for (size_t b = 0; b < marked.size(); ++b) {
+        o("    if (full & (1ull << %zu)) {\n", b);
+        emit_full(marked[b], "      ", false);
+        o("    }\n");
+      }
       o("  }\n");
     }
   }

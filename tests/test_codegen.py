@@ -24,9 +24,10 @@ def test_source_spells_out_the_network():
     # the rates near the attempt's reference temperature: one small-delta
     # update per reaction, with the full exponent as its fallback
     assert len(re.findall(r"rate_near\(w\.kp\[\d+\], de\)", src)) == net.R
-    assert len(re.findall(r"^    e = rate_exponent\(", src, re.M)) == net.R
+    assert len(re.findall(r"^      e = rate_exponent\(", src, re.M)) == net.R
+    assert src.count("else full |= 1ull << ") == net.R     # fallbacks grouped apart
     assert len(re.findall(r"^  w\.k\[\d+\] = exp_tang\(e\)", src, re.M)) == net.R
-    assert len(re.findall(r"^    w\.k\[\d+\] = exp_tang\(e\)", src, re.M)) == net.R
+    assert len(re.findall(r"^      w\.k\[\d+\] = exp_tang\(e\)", src, re.M)) == net.R
     assert len(re.findall(r"w\.g\[\d+\] = rate_dlog\(", src)) == net.R
     a = net.coeffs[5]
     assert float.hex(float(a[0])).replace("0x", "") in src.replace("0x", "")
