@@ -7,7 +7,7 @@ device the calls raise.
 
     net = Network(spec)                       # compile a network
     out = burn(net, Y0, T9, rho, t_end, rtol, atol)   # torch CUDA float64
-    Y, T9, E = Burn.apply(Y0, T9, rho, ln_mult, net, t_end, rtol, atol)
+    Y, T9, E, counters, status = Burn.apply(Y0, T9, rho, ln_mult, net, t_end, rtol, atol)
 """
 from __future__ import annotations
 
@@ -441,8 +441,9 @@ def _autograd():
     import torch
 
     class Burn(torch.autograd.Function):
-        """(Y0, T9, rho, ln_mult) -> (Y, T9, E) with a discrete-adjoint
-        backward.  ln_mult may be [R] (shared) or [Z, R]; its gradient is
+        """(Y0, T9, rho, ln_mult) -> (Y, T9, E, counters, status) with a
+        discrete-adjoint backward (counters and status are not
+        differentiable).  ln_mult may be [R] (shared) or [Z, R]; its gradient is
         d/d ln(rate multiplier) of every reaction."""
 
         @staticmethod
