@@ -59,9 +59,11 @@ def test_source_arguments_checked():
     assert rc == -1 and n.value > 1000
 
 
-def test_specialized_kernel_compiles_for_sm103a():
+@pytest.mark.parametrize("name", ["chain13_heat", "chain13", "chain13_heat_ap",
+                                  "chain13_heat_scr", "chain13_heat_tab"])
+def test_specialized_kernel_compiles_for_sm103a(name):
     try:
-        log = nb.specialize_compile(gen.network("chain13_heat"), 0)
+        log = nb.specialize_compile(gen.network(name), 0)
     except nb.NetburnError as e:
         if "libnvrtc not found" in str(e):
             pytest.skip("no run-time compiler in this image")

@@ -74,3 +74,28 @@ def test_multi_network_options_and_empty_set():
         nb.burn_multi([a] * 13, s["t_end"], s["rtol"], s["atol"])
     with pytest.raises(nb.NetburnError):
         nb.burn_multi([a], s["t_end"], -1.0, s["atol"])
+
+
+def test_multi_network_batch_with_screening_and_tables():
+    # screened (per-set plasma parameters), tabulated and effective-rate
+    # networks in one launch: each set as its single-network burn
+    nb, torch = _mods()
+    sets, specs = [], []
+    for name, Z in (("chain13_heat_scr", 300), ("chain13_heat_tab", 300),
+                    ("chain13_heat_ap", 200)):
+        net, z, s = gen.problem(name, Z)
+        t = {k: torch.from_numpy(v).cuda() for k, v in z.items()}
+        d = dict(net=nb.Network(net), Y0=t["Y"], T9=t["T9"], rho=t["rho"])
+        if "zeta" in t:
+            d["zeta"] = t["zeta"]
+        sets.append(d)
+        specs.append(s)
+    s0 = specs[0]
+    outs = nb.burn_multi(sets, s0["t_end"], s0["rtol"], s0["atol"])
+    torch.cuda.synchronize()
+    for d, out in zip(sets, outs):
+        ref = nb.burn(d["net"], d["Y0"], d["T9"], d["rho"], s0["t_end"], s0["rtol"],
+                      s0["atol"], specialize="generic", zeta=d.get("zeta"))
+        torch.cuda.synchronize()
+        assert int((out.status == 0).sum()) == d["Y0"].shape[0]
+        _equal(out, ref)
