@@ -370,7 +370,10 @@ def run_native(args):
             "e2e": None if not e2e_t else {"value": Z / statistics.mean(e2e_t), "unit": "zone-burns/s",
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                     "path": "nb_burn_batch_host (pinned host buffers, copies inside)"},
-            "gpu_launches": args.steps,
+            # per step: the burn kernel, plus the longest-first pre-pass
+            # (k_burn_estimate) whenever there is more than one zone; the
+            # CUB sort kernels between them are library code
+            "gpu_launches": args.steps * (2 if Z > 1 else 1),
             "clocks": clk,
             "plain_launch": None if not plain_ms else {
                 "value": Z / (statistics.mean(plain_ms) * 1e-3),
