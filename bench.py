@@ -335,6 +335,8 @@ def run_native(args):
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "kernel": kname,
+                "timed": ("CUDA events around each step: the burn kernel, 99.9 % of the "
+                          "step's device time, plus the longest-first pre-pass and sort"),
                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2070 MHz",
                 "flops_per_launch": ops["flops"],
                 "special_functions_per_launch": ops["special"],
