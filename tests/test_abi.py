@@ -86,3 +86,14 @@ def test_package_refuses_without_gpu():
     import paper_2312_02836_gb300 as nb
     with pytest.raises(nb.NetburnError):
         nb.Network(gen.network("chain13"))
+
+
+def test_multi_network_argument_checks_on_host():
+    # set counts and tolerances are checked before any device work
+    lib = _abi.load()
+    sets = (_abi.BurnSet * 13)()
+    assert lib.nb_burn_multi(0, sets, 1.0, 1e-8, 1e-12, None, None) == -1
+    assert lib.nb_burn_multi(13, sets, 1.0, 1e-8, 1e-12, None, None) == -1
+    assert lib.nb_burn_multi(1, None, 1.0, 1e-8, 1e-12, None, None) == -1
+    assert lib.nb_burn_multi(1, sets, 1.0, -1e-8, 1e-12, None, None) == -1
+    assert lib.nb_burn_multi(1, sets, float("nan"), 1e-8, 1e-12, None, None) == -1
