@@ -59,7 +59,7 @@ def _check(expect, got, rtol, scale=None, out_mag=0.0, abs_floor=0.0):
 
 
 @pytest.mark.parametrize("name,Z", [("net48_adjoint", 24), ("chain13_heat", 48),
-                                    ("chain13_heat_scr", 32)])
+                                    ("chain13_heat_scr", 32), ("chain13_heat_ap", 24)])
 def test_adjoint_matches_forward_sensitivity(name, Z):
     nb, torch = nb_mod()
     net, z, s = gen.problem(name, Z)
