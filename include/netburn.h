@@ -178,26 +178,24 @@ typedef struct {
                                generic kernel; 1..3 the specialised kernel
                                with that storage variant (NB_E_COMPILE when it
                                cannot be built).  Ignored with ws_in_shared
-                               > 0 and by nb_burn_batch_noalloc. */
+                               > 0 and by nb_burn_batch_noalloc (always the
+                               generic kernel). */
   const double* t_end_zone; /* [Z] device array of per-zone end times, or NULL
                                (every zone burns to t_end): operator-split use,
                                each zone burning for its own hydro step.
                                A negative or non-finite entry gives that zone
-                               NB_Z_NONFINITE.  nb_burn_batch and
-                               nb_burn_batch_host (a device pointer there too);
-                               ignored by nb_burn_batch_noalloc. */
+                               NB_Z_NONFINITE.  Every burn entry point (a
+                               device pointer in nb_burn_batch_host too). */
   double time_budget_s;     /* > 0: device watchdog.  Every lane reads the GPU
                                timer between step attempts; once the budget,
                                counted from the start of its block, has run
                                out it ends its zone with NB_Z_TIMEOUT and
                                ends every zone it claims after that the same
-                               way, so the call always finishes.  0: none.
-                               Ignored by nb_burn_batch_noalloc. */
+                               way, so the call always finishes.  0: none. */
   const double* zeta_zone;  /* [Z] device array of per-zone plasma parameters
                                for screening, or NULL (no screening).  A
                                negative or non-finite entry gives that zone
-                               NB_Z_NONFINITE.  Ignored by
-                               nb_burn_batch_noalloc. */
+                               NB_Z_NONFINITE. */
 } nb_options;
 
 #define NB_KERNEL_PERSISTENT 0  /* lane-per-zone, device work queue */
@@ -274,13 +272,20 @@ int nb_burn_adjoint(nb_net net, void* tape, int32_t K, const double* gY,
  *    of zones in flight is capped so that their workspace fits; any Z works.
  *    NB_E_TOO_LARGE when not even one block of threads_per_block zones fits
  *    (a network whose per-zone workspace exceeds the array).
+ *  - Options: those of nb_burn_batch (per-zone end times, plasma
+ *    parameters, watchdog, launch shape), except that threads_per_block is
+ *    at most 128 (NB_E_ARG beyond) and specialize and ws_in_shared are
+ *    ignored: this entry point always runs the generic kernel, so its bits
+ *    are those nb_burn_batch gives with specialize = -1.
  *  - Set-up: the first call on each device looks up the array's device
- *    address (cudaGetSymbolAddress) with that device current; make that
- *    first call before any stream capture on the device.
+ *    address (cudaGetSymbolAddress) with that device current and keeps it
+ *    for the life of the process; make that first call before any stream
+ *    capture on the device.  A cudaDeviceReset discards the array and makes
+ *    the kept address stale: do not use this entry point after a reset.
  *  - All calls share the one array: calls that can overlap on the GPU (on
  *    different streams, or from several host threads) race and corrupt each
- *    other's results.  Serialise them.  Each call zeroes the counter itself.
- *  - ws_in_shared is ignored (the workspace is always the fixed array). */
+ *    other's results.  Serialise them.  Each call zeroes the counter itself;
+ *    the workspace needs no clearing (every zone initialises its own). */
 #define NB_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
 int nb_burn_batch_noalloc(nb_net net, int64_t Z, const double* Y0,
                           const double* T9_0, const double* rho, double t_end,
@@ -356,14 +361,6 @@ int nb_specialize_compile(const nb_topology* topo, const double* coeffs,
  * its error bound; the paper has no counterpart.  Asynchronous on stream. */
 int nb_exp_eval(const double* x, double* y_tang, double* y_lib, int64_t n,
                 void* stream);
-
-/* FP64 pipe microbenchmark (a hardware measurement; the paper has no
- * counterpart).  Runs 8 independent DFMA chains per thread on
- * blocks_per_sm x SMs blocks of 256 threads, with only `active_lanes` of
- * each warp working, and returns the useful FP64 rate in TFLOP/s (an FMA
- * counted as 2).  Synchronous; allocates and frees its own output buffer. */
-int nb_probe_fp64(int32_t active_lanes, int32_t iters, int32_t blocks_per_sm,
-                  double* tflops_useful, double* ms);
 
 const char* nb_strerror(int code);
 

@@ -22,7 +22,7 @@ from ._abi import (COUNTER_NAMES, KERNEL_PERSISTENT, KERNEL_PLAIN, NCOUNT,
 
 __all__ = ["Network", "specialized_source", "specialize_compile", "burn", "burn_multi", "burn_host", "BurnGraph", "Tape", "adjoint", "Burn",
            "BurnResult", "NetburnError", "COUNTER_NAMES", "ZONE_STATUS",
-           "KERNEL_PERSISTENT", "KERNEL_PLAIN", "library_path", "probe_fp64"]
+           "KERNEL_PERSISTENT", "KERNEL_PLAIN", "library_path"]
 
 
 def library_path() -> str:
@@ -385,15 +385,6 @@ class Tape:
         self.recorded = dict(Z=Z, per_zone=(ln_mult is not None and ln_mult.dim() == 2),
                              t_end=t_end, rtol=rtol, atol=atol)
 
-    def specialize(self, variant: int = 0) -> str:
-        """Build the network-specialised kernel now (nb_net_specialize);
-        returns the compiler log."""
-        log = C.create_string_buffer(1 << 16)
-        rc = _abi.load().nb_net_specialize(self.handle, int(variant), log, len(log))
-        if rc != _abi.NB_OK:
-            raise NetburnError("nb_net_specialize: " + log.value.decode(errors="replace"))
-        return log.value.decode(errors="replace")
-
     def close(self):
         if getattr(self, "_h", None) is not None:
             _abi.load().nb_tape_free(self._h)
@@ -481,17 +472,6 @@ def _autograd():
             return dY0, dT0, None, g_lm, None, None, None, None, None
 
     return Burn
-
-
-def probe_fp64(active_lanes: int = 32, iters: int = 4096, blocks_per_sm: int = 4):
-    """Measured FP64 rate of the current GPU (TFLOP/s, FMA = 2 flops) with
-    `active_lanes` working lanes per warp."""
-    _torch()
-    tf = C.c_double(0.0)
-    ms = C.c_double(0.0)
-    _abi.check(_abi.load().nb_probe_fp64(active_lanes, iters, blocks_per_sm,
-                                         C.byref(tf), C.byref(ms)), "nb_probe_fp64")
-    return tf.value
 
 
 class _LazyBurn:

@@ -27,7 +27,7 @@ EXPORTS = ("nb_net_load", "nb_net_free", "nb_net_get_info", "nb_default_options"
            "nb_tape_steps", "nb_burn_adjoint", "nb_burn_batch_noalloc",
            "nb_burn_multi", "nb_net_specialize", "nb_specialize_source",
            "nb_specialize_compile",
-           "nb_exp_eval", "nb_probe_fp64", "nb_strerror")
+           "nb_exp_eval", "nb_strerror")
 
 
 class Topology(C.Structure):
@@ -111,8 +111,6 @@ def load(build_if_needed: bool = True):
         lib.nb_specialize_compile.restype = C.c_int
         lib.nb_exp_eval.argtypes = [P, P, P, I64, P]
         lib.nb_exp_eval.restype = C.c_int
-        lib.nb_probe_fp64.argtypes = [I32, I32, I32, P, P]
-        lib.nb_probe_fp64.restype = C.c_int
         lib.nb_strerror.argtypes = [C.c_int]
         lib.nb_strerror.restype = C.c_char_p
         for name in ("nb_net_load", "nb_net_free", "nb_net_get_info",

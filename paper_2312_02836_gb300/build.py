@@ -9,7 +9,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libnetburn.so")
-SOURCES = ["burn.cu", "adjoint.cu", "noalloc.cu", "multi.cu", "probe.cu", "netload.cpp",
+SOURCES = ["burn.cu", "adjoint.cu", "noalloc.cu", "multi.cu", "expcheck.cu", "netload.cpp",
            "codegen.cpp"]
 HEADERS = ["blob.h", "device.cuh", "integrator.cuh", "host.h", "expf64.cuh", "codegen.h"]
 # headers the run-time compiler needs, embedded as text into the library

@@ -85,7 +85,7 @@ extern "C" int nb_burn_batch_noalloc(nb_net net, int64_t Z, const double* Y0,
   nb_options o;
   nb_default_options(&o);
   if (opt) o = *opt;
-  if (o.max_attempts <= 0) return NB_E_ARG;
+  if (o.max_attempts <= 0 || !(o.time_budget_s >= 0.0)) return NB_E_ARG;
   const int tpb = o.threads_per_block > 0 ? o.threads_per_block : 128;
   if (tpb % 32 != 0 || tpb > 128) return NB_E_ARG;
 
@@ -127,6 +127,11 @@ extern "C" int nb_burn_batch_noalloc(nb_net net, int64_t Z, const double* Y0,
   P.lnm = ln_mult; P.lnm_per_zone = ln_mult_per_zone ? 1 : 0;
   P.Y = Y; P.T9 = T9; P.E = E; P.counters = counters; P.status = status;
   P.max_attempts = o.max_attempts;
+  // the per-zone options of nb_burn_batch: read-only inputs of the claim
+  // loop, so they need no scratch
+  P.budget_ns = o.time_budget_s > 0.0 ? (unsigned long long)(o.time_budget_s * 1e9) + 1ull : 0ull;
+  P.t_end_zone = o.t_end_zone;
+  P.zeta_zone = o.zeta_zone;
   P.queue = reinterpret_cast<unsigned long long*>(scratch);
   P.ws = reinterpret_cast<double*>(static_cast<unsigned char*>(scratch) + kCounterBytes);
   cudaStream_t st = (cudaStream_t)stream;

@@ -1,12 +1,12 @@
-// probe.cu -- FP64 pipe microbenchmark for the roofline denominator.
+// fp64_probe.cu -- FP64 pipe microbenchmark: the measured denominator of the
+// burn's roofline.  Measurement infrastructure, built by the tests into its
+// own small library; the burn library does not contain it.
 //
 // Every thread runs 8 independent DFMA chains; lanes >= active_lanes leave at
 // once, so the run also shows whether idle lanes of a warp free FP64 issue
 // slots (on GB300 they do not: the per-warp cost is the same).
 #include <cuda_runtime.h>
-
-#include "expf64.cuh"
-#include "../../include/netburn.h"
+#include <stdint.h>
 
 namespace {
 
@@ -23,37 +23,24 @@ __global__ void __launch_bounds__(256) k_probe_dfma(double* out, int iters, int 
   out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
 }
 
-__global__ void k_exp_eval(const double* x, double* y_tang, double* y_lib, long long n) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  y_tang[i] = nb::exp_tang(x[i]);
-  if (y_lib) y_lib[i] = exp(x[i]);
-}
-
 }  // namespace
 
-extern "C" int nb_exp_eval(const double* x, double* y_tang, double* y_lib, int64_t n,
-                           void* stream) {
-  if (n < 0 || (n > 0 && (!x || !y_tang))) return NB_E_ARG;
-  if (n == 0) return NB_OK;
-  const int tpb = 256;
-  k_exp_eval<<<(unsigned)((n + tpb - 1) / tpb), tpb, 0, (cudaStream_t)stream>>>(x, y_tang, y_lib, n);
-  return cudaGetLastError() == cudaSuccess ? NB_OK : NB_E_CUDA;
-}
-
-extern "C" int nb_probe_fp64(int32_t active_lanes, int32_t iters, int32_t blocks_per_sm,
-                             double* tflops_useful, double* ms_out) {
+// Useful FP64 rate in TFLOP/s (an FMA counted as 2) of blocks_per_sm x SMs
+// blocks of 256 threads with active_lanes working lanes per warp.  Returns 0,
+// -1 for a bad argument, -4 for a CUDA error.  Synchronous.
+extern "C" int fp64_probe(int32_t active_lanes, int32_t iters, int32_t blocks_per_sm,
+                          double* tflops_useful, double* ms_out) {
   if (active_lanes < 1 || active_lanes > 32 || iters < 1 || blocks_per_sm < 1 ||
       blocks_per_sm > 8 || !tflops_useful)
-    return NB_E_ARG;
+    return -1;
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-    return NB_E_CUDA;
+    return -4;
   const int threads = 256;
   const int blocks = sms * blocks_per_sm;
   double* out = nullptr;
-  if (cudaMalloc(&out, sizeof(double) * blocks * threads) != cudaSuccess) return NB_E_NOMEM;
+  if (cudaMalloc(&out, sizeof(double) * blocks * threads) != cudaSuccess) return -4;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -67,9 +54,9 @@ extern "C" int nb_probe_fp64(int32_t active_lanes, int32_t iters, int32_t blocks
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(out);
-  if (err != cudaSuccess) return NB_E_CUDA;
+  if (err != cudaSuccess) return -4;
   const double lane_fma = (double)blocks * threads / 32 * active_lanes * iters * 8;
   *tflops_useful = 2.0 * lane_fma / (ms * 1e-3) / 1e12;
   if (ms_out) *ms_out = ms;
-  return NB_OK;
+  return 0;
 }
