@@ -62,7 +62,8 @@ class _Opt(C.Structure):
     _fields_ = [("rtol", C.c_double), ("atol", C.c_double), ("t_end", C.c_double),
                 ("max_attempts", C.c_int32), ("newton_tol", C.c_double),
                 ("newton_maxit", C.c_int32), ("fixed_h", C.c_double),
-                ("fixed_order", C.c_int32), ("max_order", C.c_int32)]
+                ("fixed_order", C.c_int32), ("max_order", C.c_int32),
+                ("variant", C.c_int32)]
 
 
 def _load():
@@ -150,10 +151,21 @@ def _net(net):
     return net if isinstance(net, Network) else Network(net)
 
 
+# rounding variants of the oracle (bits of ``variant``): equally valid
+# orderings of the same arithmetic, used to measure how far rounding alone
+# moves a burn.  SUM_REVERSE: sums in decreasing index order; LU_REVERSE: the
+# index-reversed Newton matrix is factored; ULP: exp, log and cbrt one ulp
+# off; STEP_EXP: the step-size factor through exp and log instead of pow.
+VARIANT_SUM_REVERSE, VARIANT_LU_REVERSE, VARIANT_ULP, VARIANT_STEP_EXP = 1, 2, 4, 8
+# the set a parity check measures the oracle's own spread with: each
+# variant alone and all of them at once
+VARIANTS = (VARIANT_SUM_REVERSE, VARIANT_LU_REVERSE, VARIANT_ULP, VARIANT_STEP_EXP, 15)
+
+
 def _opts(t_end, rtol, atol, max_attempts=500000, newton_tol=1e-3,
-          newton_maxit=4, fixed_h=0.0, fixed_order=0, max_order=5):
+          newton_maxit=4, fixed_h=0.0, fixed_order=0, max_order=5, variant=0):
     return _Opt(rtol, atol, t_end, max_attempts, newton_tol, newton_maxit,
-                fixed_h, fixed_order, max_order)
+                fixed_h, fixed_order, max_order, variant)
 
 
 def rate_factors(net, T9, rho, ln_mult=None, zeta=0.0, ye=1.0):

@@ -74,6 +74,17 @@
  * x_{n+1}:  (alpha_0 I - h J(x_{n+1})) s_{n+1} = -sum_{j>=1} alpha_j s_{n+1-j}
  * + h df/dtheta.
  *
+ * Rounding variants (ora_options.variant, 0 = the oracle as described):
+ * equally valid orderings of the same arithmetic, for measuring how far
+ * rounding alone moves a burn.  Bit 1 takes every sum over reactions, over
+ * species and over the seven fit terms in decreasing index order; bit 2
+ * factors the index-reversed Newton matrix (partial pivoting kept); bit 4
+ * moves every exp, log and cbrt result by one ulp, up or down by the last
+ * bit of the argument (another libm of the same accuracy); bit 8 computes the
+ * step-size factor 0.9 E^(-1/(q+1)) as 0.9 exp(-ln(E)/(q+1)).  They change no
+ * rule of the method, only the order and the last bits of its floating-point
+ * operations.
+ *
  * Build: gcc -O2 -std=c11 -ffp-contract=off -fPIC -shared oracle.c -lm -lpthread
  * (no FMA contraction, so x86-64 and aarch64 hosts give the same bits).
  */
@@ -122,7 +133,32 @@ typedef struct {
     double fixed_h;             /* > 0: constant step, no error test */
     int32_t fixed_order;        /* > 0: order never changes from this value */
     int32_t max_order;          /* KMAX unless smaller */
+    int32_t variant;            /* rounding variant bits (header), 0 = none */
 } ora_options;
+
+enum { VAR_SUM_REVERSE = 1, VAR_LU_REVERSE = 2, VAR_ULP = 4, VAR_STEP_EXP = 8 };
+
+/* the rounding variant of the zone this thread is burning (0 outside a burn) */
+static _Thread_local int g_variant = 0;
+
+/* q-th index of a sum over [0, m): increasing, or decreasing under the
+   reversed-sum variant */
+static int sum_index(int q, int m) {
+    return (g_variant & VAR_SUM_REVERSE) ? m - 1 - q : q;
+}
+
+/* a transcendental result y = fn(x), moved by one ulp under the ulp variant:
+   up when the last bit of x is set, else down */
+static double ulp_variant(double y, double x) {
+    if (!(g_variant & VAR_ULP) || !isfinite(y) || y == 0.0) return y;
+    uint64_t b;
+    memcpy(&b, &x, sizeof b);
+    return nextafter(y, (b & 1u) ? INFINITY : -INFINITY);
+}
+
+static double v_exp(double x) { return ulp_variant(exp(x), x); }
+static double v_log(double x) { return ulp_variant(log(x), x); }
+static double v_cbrt(double x) { return ulp_variant(cbrt(x), x); }
 
 /* ------------------------------------------------------------------ */
 /* model                                                               */
@@ -175,8 +211,8 @@ static double table_lnl(const ora_network* net, int tb, double lrye, double T9, 
 
 void ora_rate_factors(const ora_network* net, double T9, double rho, double zeta,
                       double ye, const double* ln_mult, double* k, double* g) {
-    double t13 = cbrt(T9);
-    double phi[7] = {1.0, 1.0 / T9, 1.0 / t13, t13, T9, T9 * t13 * t13, log(T9)};
+    double t13 = v_cbrt(T9);
+    double phi[7] = {1.0, 1.0 / T9, 1.0 / t13, t13, T9, T9 * t13 * t13, v_log(T9)};
     double dphi[7] = {0.0,
                       -1.0 / (T9 * T9),
                       -1.0 / (3.0 * T9 * t13),
@@ -187,7 +223,8 @@ void ora_rate_factors(const ora_network* net, double T9, double rho, double zeta
     for (int r = 0; r < net->R; ++r) {
         const double* a = net->coeffs + 7 * r;
         double e = 0.0, de = 0.0;
-        for (int j = 0; j < 7; ++j) {
+        for (int q = 0; q < 7; ++q) {
+            int j = sum_index(q, 7);
             e += a[j] * phi[j];
             de += a[j] * dphi[j];
         }
@@ -207,7 +244,7 @@ void ora_rate_factors(const ora_network* net, double T9, double rho, double zeta
             H = net->screen[r] * sqrt(rho * zeta) * pow(1e3 * T9, -1.5);
         e += H;
         de += -1.5 * H / T9;
-        double lam = exp(e);
+        double lam = v_exp(e);
         if (net->ap_pg && net->ap_pg[r]) {
             /* lambda = lambda_ag + lambda_ap lambda_pg / (lambda_pg + lambda_pa) */
             double ec[3], dec[3];
@@ -215,7 +252,8 @@ void ora_rate_factors(const ora_network* net, double T9, double rho, double zeta
                 const double* b = net->ap_coeffs + 21 * r + 7 * c;
                 ec[c] = 0.0;
                 dec[c] = 0.0;
-                for (int j = 0; j < 7; ++j) {
+                for (int q = 0; q < 7; ++q) {
+                    int j = sum_index(q, 7);
                     ec[c] += b[j] * phi[j];
                     dec[c] += b[j] * dphi[j];
                 }
@@ -223,14 +261,14 @@ void ora_rate_factors(const ora_network* net, double T9, double rho, double zeta
             /* the alpha capture screens the (a,p) channel as it does the direct one */
             ec[0] += H;
             dec[0] += -1.5 * H / T9;
-            double l_ag = lam, l_ap = exp(ec[0]), l_pg = exp(ec[1]), l_pa = exp(ec[2]);
+            double l_ag = lam, l_ap = v_exp(ec[0]), l_pg = v_exp(ec[1]), l_pa = v_exp(ec[2]);
             double frac = l_pg / (l_pg + l_pa);
             double via_p = l_ap * frac;
             lam = l_ag + via_p;
             /* d ln lambda / dT9: d frac/dT9 = frac (1 - frac) (g_pg - g_pa) */
             de = (l_ag * de + via_p * (dec[0] + (1.0 - frac) * (dec[1] - dec[2]))) / lam;
         }
-        k[r] = s * exp(p) * rp * lam;
+        k[r] = s * v_exp(p) * rp * lam;
         if (g) g[r] = de;
     }
 }
@@ -272,7 +310,7 @@ static void reaction_terms(const ora_network* net, const double* x,
 
 static double heat_capacity(const ora_network* net, const double* x) {
     double sy = 0.0;
-    for (int i = 0; i < net->N; ++i) sy += x[i];
+    for (int q = 0; q < net->N; ++q) sy += x[sum_index(q, net->N)];
     double T9 = x[net->N];
     return 1.5 * sy + 1e-3 * T9 * T9 * T9;
 }
@@ -285,11 +323,13 @@ static void rhs_given_k(const ora_network* net, const rxn_species* L,
     int N = net->N, R = net->R;
     reaction_terms(net, x, k, Rr);
     for (int i = 0; i < N; ++i) f[i] = 0.0;
-    for (int r = 0; r < R; ++r)
+    for (int qr = 0; qr < R; ++qr) {
+        int r = sum_index(qr, R);
         for (int q = 0; q < L[r].cnt; ++q) f[L[r].sp[q]] += L[r].c[q] * Rr[r];
+    }
     double ed = 0.0;
     if (net->Q)
-        for (int r = 0; r < R; ++r) ed += net->Q[r] * Rr[r];
+        for (int qr = 0; qr < R; ++qr) ed += net->Q[sum_index(qr, R)] * Rr[sum_index(qr, R)];
     if (edot) *edot = ed;
     if (net->self_heating) f[N] = ed / heat_capacity(net, x);
 }
@@ -332,7 +372,8 @@ static void jacobian_given_k(const ora_network* net, const rxn_species* L,
                              double* J, double* Rr) {
     int N = net->N, R = net->R, n = N + (net->self_heating ? 1 : 0);
     memset(J, 0, sizeof(double) * n * n);
-    for (int r = 0; r < R; ++r) {
+    for (int qr = 0; qr < R; ++qr) {
+        int r = sum_index(qr, R);
         int js[3];
         int m = distinct_reactants(net, r, js);
         for (int a = 0; a < m; ++a) {
@@ -345,16 +386,20 @@ static void jacobian_given_k(const ora_network* net, const rxn_species* L,
     reaction_terms(net, x, k, Rr);
     double cv = heat_capacity(net, x);
     double ed = 0.0, dedT = 0.0;
-    for (int r = 0; r < R; ++r) {
+    for (int qr = 0; qr < R; ++qr) {
+        int r = sum_index(qr, R);
         ed += net->Q[r] * Rr[r];
         dedT += net->Q[r] * Rr[r] * g[r];
     }
     double fT = ed / cv;
-    for (int r = 0; r < R; ++r)
+    for (int qr = 0; qr < R; ++qr) {
+        int r = sum_index(qr, R);
         for (int q = 0; q < L[r].cnt; ++q)
             J[L[r].sp[q] * n + N] += L[r].c[q] * Rr[r] * g[r];
+    }
     /* T row: d edot / dY_j, accumulated over r in increasing order */
-    for (int r = 0; r < R; ++r) {
+    for (int qr = 0; qr < R; ++qr) {
+        int r = sum_index(qr, R);
         int js[3];
         int m = distinct_reactants(net, r, js);
         for (int a = 0; a < m; ++a)
@@ -399,8 +444,23 @@ void ora_jacobian(const ora_network* net, const double* x, double T9, double rho
 /* dense linear algebra (textbook LU with partial pivoting)            */
 /* ------------------------------------------------------------------ */
 
+/* reverse the index order of an n x n matrix in place: A[i][j] <->
+   A[n-1-i][n-1-j] (the reversed-LU variant factors this matrix) */
+static void reverse_matrix(double* A, int n) {
+    for (int e = 0; e < n * n / 2; ++e) {
+        double t = A[e]; A[e] = A[n * n - 1 - e]; A[n * n - 1 - e] = t;
+    }
+}
+
+static void reverse_vector(double* b, int n) {
+    for (int i = 0; i < n / 2; ++i) {
+        double t = b[i]; b[i] = b[n - 1 - i]; b[n - 1 - i] = t;
+    }
+}
+
 /* factor A (n x n, row-major) in place; returns 0 or -1 if singular */
 static int lu_factor(double* A, int* piv, int n) {
+    if (g_variant & VAR_LU_REVERSE) reverse_matrix(A, n);
     for (int c = 0; c < n; ++c) {
         int p = c;
         double best = fabs(A[c * n + c]);
@@ -422,6 +482,7 @@ static int lu_factor(double* A, int* piv, int n) {
 }
 
 static void lu_solve(const double* A, const int* piv, int n, double* b) {
+    if (g_variant & VAR_LU_REVERSE) reverse_vector(b, n);
     for (int c = 0; c < n; ++c) {
         int p = piv[c];
         if (p != c) { double t = b[c]; b[c] = b[p]; b[p] = t; }
@@ -436,6 +497,7 @@ static void lu_solve(const double* A, const int* piv, int n, double* b) {
         for (int j = i + 1; j < n; ++j) s -= A[i * n + j] * b[j];
         b[i] = s / A[i * n + i];
     }
+    if (g_variant & VAR_LU_REVERSE) reverse_vector(b, n);
 }
 
 /* ------------------------------------------------------------------ */
@@ -475,7 +537,8 @@ void ora_extrapolate(int q, int n, const double* t_pts, const double* x_pts,
 
 static double wnorm(int n, const double* v, const double* w) {
     double s = 0.0;
-    for (int i = 0; i < n; ++i) {
+    for (int qi = 0; qi < n; ++qi) {
+        int i = sum_index(qi, n);
         double q = v[i] / w[i];
         s += q * q;
     }
@@ -576,9 +639,15 @@ static void push_history(work_t* W, int n, int* nh, double t, const double* x, d
     if (*nh < HMAX) (*nh)++;
 }
 
+/* 0.9 E^(-1/(q+1)) */
+static double err_power(double E, int q) {
+    if (g_variant & VAR_STEP_EXP) return 0.9 * exp(-log(E) / (q + 1));
+    return 0.9 * pow(E, -1.0 / (q + 1));
+}
+
 static double step_factor(double E, int q) {
     if (!(E > 0.0)) return 5.0;
-    return 0.9 * pow(E, -1.0 / (q + 1));
+    return err_power(E, q);
 }
 
 /* E_q after an accepted step: the newest point is W->xh[0] (time th[0]),
@@ -599,6 +668,7 @@ static int burn_zone(const ora_network* net, const ora_options* opt,
     const int has_E = net->Q != NULL;
     const double t_end = opt->t_end, rtol = opt->rtol, atol = opt->atol;
     const int kmax = opt->max_order > 0 && opt->max_order < KMAX ? opt->max_order : KMAX;
+    g_variant = opt->variant;
     zone_ctx z = {net, rho, T9_0, ln_mult, cnt, zeta, electron_fraction(net, Y0)};
     double* f0 = malloc(sizeof(double) * n);   /* f(x_0), for the first predictor */
     memset(cnt, 0, sizeof(int32_t) * C_COUNT);
@@ -727,7 +797,7 @@ static int burn_zone(const ora_network* net, const ora_options* opt,
         double err = wnorm(n, W->tmp, W->w);
         if (opt->fixed_h <= 0.0 && !(err <= 1.0)) {
             cnt[C_REJ_ERR]++;
-            double fac = isfinite(err) ? 0.9 * pow(err, -1.0 / (kk + 1)) : 0.2;
+            double fac = isfinite(err) ? err_power(err, kk) : 0.2;
             h *= fac > 0.2 ? fac : 0.2;
             continue;
         }
@@ -786,6 +856,7 @@ done:
     for (int i = 0; i < N; ++i) Y_out[i] = W->xh[i];
     if (T9_out) *T9_out = net->self_heating ? W->xh[N] : T9_0;
     if (E_out) *E_out = W->Eh[0];
+    g_variant = 0;
     return status;
 }
 

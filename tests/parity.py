@@ -1,90 +1,159 @@
 """Comparison of GPU burns with the CPU oracle (shared by the GPU tests,
 ``__graft_entry__.smoke`` and the benchmark's sampled check).
 
-The bar, per zone:
-  * status equal; accepted-step counts within 2 of each other;
-  * zones whose accepted-step counts agree: every species within
-    1e-9 |Y_oracle| + max(1e-5 atol, 1e-15 max_j |Y_oracle,j|), T9 and E
-    within 1e-9 relative (+1e-12 absolute for E);
-  * zones whose counts differ by 1 or 2 took a different (equally valid)
-    step sequence; they must agree to the integration tolerance,
-    1e-4 |Y| + atol, and be rare (< 1% of zones).
-The method resolves a species only to its weight w = atol + rtol |Y| (the
-Newton test stops at 1e-3 w, the error test at w), so species near or below
-atol agree between two correct implementations only to a fraction of atol,
-hence the 1e-5 atol absolute floor (1e-17 at the workloads' atol = 1e-12).
-A species' rate of change is a sum of terms proportional to the zone's large
-abundances, so its absolute rounding error follows theirs, not its own size:
-the floor is at least a few ulps of the zone's largest abundance,
-1e-15 max_j |Y_j| (2.5e-16 when Y_0 = 1/4 dominates).
-Networks with tabulated rates take the wider same-step bar TABULATED below.
+The target bar, per zone and species: |Y_gpu - Y_ora| <= 1e-9 |Y_ora| where
+|Y_ora| > 1e-20, else <= 1e-25 absolute; T9 and E within 1e-9 relative;
+accepted-step counts within 2.
+
+That bar is stricter than the method resolves some entries, and how much
+stricter is measured, not assumed: the oracle is run again under its
+rounding variants (``oracle.VARIANTS``: sums in reversed order, the Newton
+matrix factored in reversed index order, exp/log/cbrt one ulp off, the
+step-size factor through exp/log instead of pow, and all of them at once).
+Each variant is an equally valid FP64 implementation of the same method, so
+how far it lands from the oracle is the oracle's own rounding noise on that
+very workload.  An entry that misses the target bar passes only when its
+deviation is within twice that measured noise:
+
+  * spread P = max over variants, zones and species of |Y_var - Y_ora| / w,
+    w = atol + rtol |Y_ora| (the weight the method resolves a species to),
+    over the zones where the variant took the oracle's step count; every
+    entry must satisfy  |Y_gpu - Y_ora| <= max(target, 2 P w);
+  * T9 and E likewise: target, or twice the variants' largest relative
+    deviation;
+  * a zone may take a different number of accepted steps than the oracle
+    only by up to max(2, the variants' own largest difference), and such
+    zones may be no more than twice as many as the variants diverge on
+    (at least one).  They are held to twice the variants' spread over all
+    zones, diverged ones included;
+  * a zone's final status must equal the oracle's, except on zones where a
+    rounding variant's status differs from the oracle's too (an outcome
+    decided by rounding, e.g. a Newton iteration at the FP64 noise floor of
+    its convergence test); such zones are reported and not compared further.
+
+The factor 2 is the margin for one more independent rounding realisation
+(the GPU) against the maximum over a handful of them.  Measured spreads
+(host build of the device code vs the oracle, design notes): smooth networks
+P ~ 1e-4 (the target bar holds except for species far below atol, where the
+variants miss it as often as the GPU does); tabulated networks P ~ 5-15,
+because the kinks of a piecewise-linear ln(lambda) make the step-size
+sequence, and so the discretisation error, sensitive to rounding.
 """
 from __future__ import annotations
 
 import numpy as np
 
-
-# Networks with tabulated rates: ln lambda is piecewise linear in T9, so the
-# right-hand side has kinks at the table's temperatures.  Where a step
-# straddles a kink its error estimate, and so the step sizes around it,
-# depend sharply on where it lands, and two implementations that differ at
-# rounding level agree only to the method's own resolution: each entry to
-# its weight w = atol + rtol |Y| (the error test), T9 and E to 1e-6
-# relative.  Measured over 2048 zones (host run of the device code against
-# the oracle): 0.16 of this bar at most, T9 4e-8, 0.6 % of zones on a
-# different step sequence.  Near a kink the error test can accept or reject
-# a step on rounding, each flip shifting the step sequence; a zone crosses at
-# most the grid's 12 temperatures, so accepted-step counts may differ by up to
-# 12 (such zones are still held to the integration tolerance).  Measured on
-# the GPU: 3.
-TABULATED = dict(same_rel=1e-6, same_w=1.0, scalar_rel=1e-6, max_diverged_frac=0.03,
-                 max_step_diff=12)
+KEYS = ("Y", "T9", "E", "counters", "status")
 
 
-def compare(gpu: dict, ora: dict, atol: float, max_step_diff: int = 2,
-            max_diverged_frac: float = 0.01, same_rel: float = 1e-9, same_w: float = 0.0,
-            scalar_rel: float = 1e-9, rtol: float = 1e-8) -> dict:
+def _literal_fail(a, b):
+    err = np.abs(a - b)
+    return np.where(np.abs(b) > 1e-20, err > 1e-9 * np.abs(b), err > 1e-25)
+
+
+def oracle_spread(ora: dict, variants, atol: float, rtol: float) -> dict:
+    """How far the oracle's rounding variants land from the oracle: the
+    measured noise of an equally valid FP64 implementation."""
+    Yo = np.asarray(ora["Y"])
+    w = atol + rtol * np.abs(Yo)
+    acc = np.asarray(ora["counters"])[:, 0].astype(np.int64)
+    ok = np.asarray(ora["status"]) == 0
+    sp = dict(P_same=0.0, P_all=0.0, T9=0.0, E=0.0, max_step_diff=0, max_diverged=0,
+              literal_fail_frac=0.0, n=len(variants),
+              status_sensitive=np.zeros(Yo.shape[0], dtype=bool))
+    for v in variants:
+        sp["status_sensitive"] |= np.asarray(v["status"]) != np.asarray(ora["status"])
+        dv = np.asarray(v["counters"])[:, 0].astype(np.int64) - acc
+        same = ok & (dv == 0) & (np.asarray(v["status"]) == 0)
+        both = ok & (np.asarray(v["status"]) == 0)
+        d = np.abs(np.asarray(v["Y"]) - Yo) / w
+        if same.any():
+            sp["P_same"] = max(sp["P_same"], float(d[same].max()))
+            sp["literal_fail_frac"] = max(sp["literal_fail_frac"], float(
+                _literal_fail(np.asarray(v["Y"]), Yo)[same].mean()))
+        if both.any():
+            sp["P_all"] = max(sp["P_all"], float(d[both].max()))
+            sp["max_step_diff"] = max(sp["max_step_diff"], int(np.abs(dv[both]).max()))
+        sp["max_diverged"] = max(sp["max_diverged"], int((both & (dv != 0)).sum()))
+        for key in ("T9", "E"):
+            if ora.get(key) is not None and v.get(key) is not None and same.any():
+                b = np.asarray(ora[key])
+                r = np.abs(np.asarray(v[key]) - b) / np.maximum(np.abs(b), 1e-300)
+                sp[key] = max(sp[key], float(r[same].max()))
+    return sp
+
+
+def compare(gpu: dict, ora: dict, atol: float, rtol: float = 1e-8, spread: dict | None = None,
+            variants=None) -> dict:
+    """Assert the parity bar (module docstring) and return a report.  The
+    measured spread comes from ``spread`` (see oracle_spread) or is computed
+    from ``variants``; without either, only the target bar applies."""
+    if spread is None:
+        spread = oracle_spread(ora, variants or [], atol, rtol)
     Yg, Yo = np.asarray(gpu["Y"]), np.asarray(ora["Y"])
     sg, so = np.asarray(gpu["status"]), np.asarray(ora["status"])
     cg, co = np.asarray(gpu["counters"]), np.asarray(ora["counters"])
     Z = Yo.shape[0]
-    report = {"zones": Z}
-    bad = np.where(sg != so)[0]
+    rep = {"zones": Z, "oracle_spread": {k: spread[k] for k in
+                                         ("P_same", "P_all", "max_step_diff", "max_diverged",
+                                          "literal_fail_frac", "T9", "E", "n")}}
+    sens = spread.get("status_sensitive", np.zeros(Z, dtype=bool))
+    bad = np.where((sg != so) & ~sens)[0]
     assert bad.size == 0, f"status differs in zones {bad[:10]}: gpu {sg[bad[:10]]} oracle {so[bad[:10]]}"
-    ok = so == 0
+    rep["status_differs_rounding_decided"] = [int(z) for z in np.where(sg != so)[0]]
+    rep["oracle_spread"]["status_sensitive_zones"] = int(sens.sum())
+    ok = (so == 0) & (sg == so)
     dacc = cg[:, 0].astype(np.int64) - co[:, 0].astype(np.int64)
-    report["max_step_diff"] = int(np.abs(dacc[ok]).max()) if ok.any() else 0
-    assert report["max_step_diff"] <= max_step_diff, \
-        f"accepted steps differ by {report['max_step_diff']}"
+    rep["max_step_diff"] = int(np.abs(dacc[ok]).max()) if ok.any() else 0
+    lim_steps = max(2, spread["max_step_diff"])
+    assert rep["max_step_diff"] <= lim_steps, \
+        f"accepted steps differ by {rep['max_step_diff']} (limit {lim_steps})"
     same = ok & (dacc == 0)
     diverged = ok & (dacc != 0)
-    report["diverged_zones"] = int(diverged.sum())
-    assert diverged.sum() <= max(1, int(max_diverged_frac * Z)), \
-        f"{diverged.sum()} of {Z} zones took a different step sequence"
-    floor = np.maximum(1e-5 * atol, 1e-15 * np.abs(Yo).max(axis=1, keepdims=True))
-    tol = same_rel * np.abs(Yo) + floor + same_w * (atol + rtol * np.abs(Yo))
+    rep["diverged_zones"] = int(diverged.sum())
+    lim_div = max(1, 2 * spread["max_diverged"])
+    assert diverged.sum() <= lim_div, \
+        f"{diverged.sum()} of {Z} zones took a different step count (limit {lim_div})"
+    w = atol + rtol * np.abs(Yo)
     err = np.abs(Yg - Yo)
-    viol = (err > tol) & same[:, None]
-    rel = np.where(np.abs(Yo) > 1e-20, err / np.maximum(np.abs(Yo), 1e-300), 0.0)
-    report["max_rel_Y"] = float(rel[same].max()) if same.any() else 0.0
-    report["max_abs_small_Y"] = float(np.where(np.abs(Yo) <= 1e-20, err, 0)[same].max()) if same.any() else 0.0
+    lit = _literal_fail(Yg, Yo)
+    rep["literal_fail_frac"] = float(lit[same].mean()) if same.any() else 0.0
+    rep["literal_fail_entries"] = int(lit[same].sum())
+    rep["max_rel_Y"] = float(np.where(np.abs(Yo) > 1e-20, err / np.maximum(np.abs(Yo), 1e-300),
+                                      0.0)[same].max()) if same.any() else 0.0
+    rep["max_err_over_w"] = float((err / w)[ok].max()) if ok.any() else 0.0
+    viol = lit & (err > 2.0 * spread["P_same"] * w) & same[:, None]
     zi = np.where(viol.any(1))[0]
-    assert zi.size == 0, (f"{zi.size} zones exceed the same-step bar, e.g. zone {zi[0]}: "
-                          f"gpu {Yg[zi[0]][viol[zi[0]]][:4]} oracle {Yo[zi[0]][viol[zi[0]]][:4]}")
+    if zi.size:
+        z0 = zi[0]
+        i0 = np.where(viol[z0])[0][0]
+        raise AssertionError(
+            f"{zi.size} same-step zones miss the bar, e.g. zone {z0} species {i0}: gpu "
+            f"{Yg[z0, i0]!r} oracle {Yo[z0, i0]!r}, |d|/w {err[z0, i0] / w[z0, i0]:.3g} > "
+            f"2 x measured oracle spread {spread['P_same']:.3g}")
     if diverged.any():
-        loose = 1e-4 * np.abs(Yo) + atol
-        zl = np.where(((err > loose) & diverged[:, None]).any(1))[0]
-        assert zl.size == 0, f"diverged zones {zl[:5]} differ beyond the integration tolerance"
-    for key, floor in (("T9", 0.0), ("E", 1e-12)):
-        if key in gpu and key in ora and gpu[key] is not None:
+        dv = (err > 1e-9 * np.abs(Yo) + 2.0 * spread["P_all"] * w) & diverged[:, None]
+        zl = np.where(dv.any(1))[0]
+        assert zl.size == 0, (f"zones {zl[:5]} took a different step count and differ beyond "
+                              f"2 x the oracle's spread ({spread['P_all']:.3g} w)")
+    for key in ("T9", "E"):
+        if gpu.get(key) is not None and ora.get(key) is not None:
             a, b = np.asarray(gpu[key]), np.asarray(ora[key])
-            e = np.abs(a - b)
-            lim = np.where(same, scalar_rel * np.abs(b) + floor, 1e-4 * np.abs(b) + 1e-8)
-            report[f"max_rel_{key}"] = float((e / np.maximum(np.abs(b), 1e-300))[ok].max()) if ok.any() else 0.0
-            zb = np.where(ok & (e > lim))[0]
+            r = np.abs(a - b) / np.maximum(np.abs(b), 1e-300)
+            rep[f"max_rel_{key}"] = float(r[ok].max()) if ok.any() else 0.0
+            lim = np.where(same, max(1e-9, 2.0 * spread[key]), 1e-4)
+            zb = np.where(ok & (r > lim) & (np.abs(a - b) > 1e-300))[0]
             assert zb.size == 0, f"{key} differs in zones {zb[:5]}: {a[zb[:5]]} vs {b[zb[:5]]}"
-    return report
+    return rep
+
+
+def oracle_with_variants(burn, *args, **kw):
+    """(oracle result, list of its rounding-variant results) for one call of
+    ``oracle.burn``-like ``burn(*args, variant=v, **kw)``."""
+    import oracle
+    base = burn(*args, **kw)
+    return base, [burn(*args, variant=v, **kw) for v in oracle.VARIANTS]
 
 
 def to_numpy(res) -> dict:
-    return {k: getattr(res, k).cpu().numpy() for k in ("Y", "T9", "E", "counters", "status")}
+    return {k: getattr(res, k).cpu().numpy() for k in KEYS}

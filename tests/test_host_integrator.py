@@ -14,7 +14,7 @@ import pytest
 import gen
 import oracle
 from paper_2312_02836_gb300 import _topology, build
-from tests.parity import TABULATED, compare
+from tests.parity import compare
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
@@ -55,10 +55,10 @@ def test_host_integrator_matches_oracle(host_lib, name, Z):
                             p(zeta), s["t_end"], s["rtol"], s["atol"],
                             p(Y), p(T9), p(E), p(cnt), p(st))
     assert rc == 0
-    o = oracle.burn(net, z["Y"], z["T9"], z["rho"], s["t_end"], s["rtol"], s["atol"],
-                    zeta=zeta)
-    bar = TABULATED if getattr(net, "tab_of", None) is not None else {}
+    run = lambda v: oracle.burn(net, z["Y"], z["T9"], z["rho"], s["t_end"], s["rtol"],
+                                s["atol"], zeta=zeta, variant=v)
+    o = run(0)
     rep = compare(dict(Y=Y, T9=T9, E=E, counters=cnt, status=st), o, s["atol"],
-                  rtol=s["rtol"], **bar)
+                  rtol=s["rtol"], variants=[run(v) for v in oracle.VARIANTS])
     assert (st == 0).all()
     print(name, rep)
