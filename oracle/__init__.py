@@ -81,7 +81,7 @@ def _load():
                                            P, P, I32, P, P]
             lib.ora_burn_batch.restype = I32
             lib.ora_burn_tape.argtypes = [P, P, P, D, D, D, P, P, P, P, P, I32, P,
-                                          P, P, P, P]
+                                          P, P, P, P, P]
             lib.ora_burn_tape.restype = I32
             lib.ora_replay.argtypes = [P, P, P, D, D, D, P, I32, P, P, D, I32, P, P]
             lib.ora_replay.restype = I32
@@ -264,7 +264,8 @@ def burn(net, Y0, T9, rho, t_end, rtol, atol, ln_mult=None, threads=0, zeta=None
 def burn_tape(net, Y0, T9, rho, t_end, rtol, atol, ln_mult=None, cap=200000,
               zeta=0.0, **opts):
     """One zone with its accepted schedule: dict(Y, T9, E, counters, status,
-    t [S+1], k [S+1], x [S+1, n], Ehist [S+1])."""
+    t [S+1], k [S+1], x [S+1, n], Ehist [S+1], hnext [S+1]); hnext[s] is the
+    step size the controller chose after accepted step s."""
     net = _net(net)
     lib = _load()
     Y0 = _f64(Y0)
@@ -277,16 +278,17 @@ def burn_tape(net, Y0, T9, rho, t_end, rtol, atol, ln_mult=None, cap=200000,
     tk = np.empty(cap, dtype=np.int32)
     tx = np.empty((cap, net.n))
     tE = np.empty(cap)
+    th = np.full(cap, np.nan)
     count = C.c_int32(0)
     o = _opts(t_end, rtol, atol, **opts)
     st = lib.ora_burn_tape(net.ptr, C.addressof(o), _p(Y0), float(T9),
                            float(rho), float(zeta), _p(lm), _p(Y), C.byref(T9o), C.byref(E),
                            _p(cnt), cap, _p(tt), _p(tk), _p(tx), _p(tE),
-                           C.byref(count))
+                           C.byref(count), _p(th))
     c = count.value
     return dict(Y=Y, T9=T9o.value, E=E.value, counters=cnt, status=st,
                 t=tt[:c].copy(), k=tk[:c].copy(), x=tx[:c].copy(),
-                Ehist=tE[:c].copy())
+                Ehist=tE[:c].copy(), hnext=th[:c].copy())
 
 
 def replay(net, Y0, T9, rho, t, k, rtol, atol, ln_mult=None, tol=1e-6,

@@ -563,6 +563,9 @@ typedef struct {
     double* x;      /* [cap * n] */
     double* E;      /* [cap] */
     int32_t count;
+    double* hnext;  /* [cap] or NULL: the step size the controller chose after
+                       accepted step s (the next attempt's h before it is cut
+                       to land on t_end) */
 } ora_tape;
 
 typedef struct {
@@ -825,6 +828,7 @@ static int burn_zone(const ora_network* net, const ora_options* opt,
         }
         if (opt->fixed_h > 0.0) {
             h = opt->fixed_h;
+            if (tape && tape->hnext && tape->count <= tape->cap) tape->hnext[tape->count - 1] = h;
             continue;
         }
         /* step size and order for the next step */
@@ -850,6 +854,8 @@ static int burn_zone(const ora_network* net, const ora_options* opt,
         if (factor > 5.0) factor = 5.0;
         if (factor >= 1.0 && factor < 1.2) factor = 1.0;
         h *= factor;
+        if (tape && tape->hnext && tape->count >= 1 && tape->count <= tape->cap)
+            tape->hnext[tape->count - 1] = h;
     }
 done:
     free(f0);
@@ -940,9 +946,10 @@ int ora_burn_tape(const ora_network* net, const ora_options* opt,
                   const double* Y0, double T9_0, double rho, double zeta,
                   const double* ln_mult, double* Y, double* T9_out, double* E,
                   int32_t* cnt, int32_t cap, double* tape_t, int32_t* tape_k,
-                  double* tape_x, double* tape_E, int32_t* tape_count) {
+                  double* tape_x, double* tape_E, int32_t* tape_count,
+                  double* tape_hnext) {
     work_t* W = work_alloc(net);
-    ora_tape tp = {cap, tape_t, tape_k, tape_x, tape_E, 0};
+    ora_tape tp = {cap, tape_t, tape_k, tape_x, tape_E, 0, tape_hnext};
     int st = burn_zone(net, opt, Y0, T9_0, rho, zeta, ln_mult, Y, T9_out, E, cnt, &tp, W);
     *tape_count = tp.count;
     work_free(W);
