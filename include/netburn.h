@@ -238,13 +238,33 @@ int nb_burn_batch_host(nb_net net, int64_t Z, const double* Y0,
                        double* E, int32_t* counters, int32_t* status,
                        const nb_options* opt, void* stream);
 
-/* Adjoint tape: per zone up to max_steps accepted steps (time, order,
- * state, energy) in device memory owned by the tape.  Synchronous. */
-int nb_tape_alloc(nb_net net, int64_t Z, int32_t max_steps, void** tape);
+/* Adjoint tape (Sec. 1 and 3: the rate sensitivity of a burn), in device
+ * memory owned by the tape.  Per zone it holds, for up to max_steps
+ * accepted steps, the schedule of every step (time t_s, step size h_s, BDF
+ * order), and states x_s, E_s only at checkpoints: the initial state and
+ * the last min(ckpt_stride, 7) states of every block of ckpt_stride steps,
+ * the BDF history window from which nb_burn_adjoint recomputes each block's
+ * states, bit for bit, in its reverse sweep.  Memory per zone is about
+ * 17 (max_steps + 1) + 8 (n + 1) (1 + 7 max_steps / ckpt_stride) bytes
+ * (n = N + self_heating).  ckpt_stride: 1 keeps every state (no
+ * recomputation); 0 takes NB_TAPE_DEFAULT_STRIDE.  Synchronous. */
+#define NB_TAPE_DEFAULT_STRIDE 16
+int nb_tape_alloc(nb_net net, int64_t Z, int32_t max_steps, int32_t ckpt_stride,
+                  void** tape);
 int nb_tape_free(void* tape);
-/* Device pointer to the accepted-step counts [Z] int32 of the last burn
- * recorded on the tape. */
+/* Device pointer to the record counts [Z] int32 (accepted steps + 1) of the
+ * last burn recorded on the tape. */
 int nb_tape_steps(void* tape, const int32_t** steps);
+/* Copy zone z's record of the last burn on the tape to HOST arrays: per
+ * record s = 0 .. count-1 (s = 0 the initial point, s >= 1 accepted step s)
+ * t [cap], h [cap] (the step size that step used; 0 for s = 0), order [cap]
+ * (its BDF order; 0 for s = 0), x [cap, n] and E [cap] (the state and energy
+ * after it where the tape keeps them, NaN elsewhere; every record with
+ * ckpt_stride 1).  Any array may be NULL.  *count receives the record
+ * count; NB_E_ARG (arrays untouched) when it exceeds cap, NB_E_TAPE when
+ * the tape holds no burn.  Waits for the device (cudaDeviceSynchronize). */
+int nb_tape_read(void* tape, int64_t z, int32_t cap, double* t, double* h,
+                 int32_t* order, double* x, double* E, int32_t* count);
 
 /* Discrete adjoint of a recorded burn (same net, same ln_mult, same
  * inputs).  K cotangent sets per zone:
@@ -253,8 +273,12 @@ int nb_tape_steps(void* tape, const int32_t** steps);
  *  dY0 [K, Z, N] or NULL, dT0 [K, Z] or NULL  device outputs
  * The schedule (step times and orders) is held fixed and the Newton
  * solutions are treated as exact: this is the exact gradient of the
- * discrete map the forward burn computed.  Zones whose forward status was
- * not NB_Z_OK get zero gradients. */
+ * discrete map the forward burn computed.  The reverse sweep takes the
+ * blocks of ckpt_stride steps last to first, recomputes each block's states
+ * from its checkpoint with the forward's own step computation (same bits),
+ * then reverses the block.  Zones whose forward status was not NB_Z_OK get
+ * zero gradients; a zone whose recomputation failed to converge (which the
+ * forward's convergence on the same inputs excludes) gets NaN. */
 int nb_burn_adjoint(nb_net net, void* tape, int32_t K, const double* gY,
                     const double* gE, const double* gT9, double* d_ln_mult,
                     double* dY0, double* dT0, void* stream);

@@ -85,7 +85,7 @@ def _load():
             lib.ora_burn_tape.restype = I32
             lib.ora_replay.argtypes = [P, P, P, D, D, D, P, I32, P, P, D, I32, P, P]
             lib.ora_replay.restype = I32
-            lib.ora_forward_sensitivity.argtypes = [P, D, D, D, P, I32, P, P, P, P, P]
+            lib.ora_forward_sensitivity.argtypes = [P, D, D, D, P, I32, P, P, P, P, I32, P, P]
             lib.ora_forward_sensitivity.restype = I32
             _lib = lib
     return _lib
@@ -155,11 +155,14 @@ def _net(net):
 # orderings of the same arithmetic, used to measure how far rounding alone
 # moves a burn.  SUM_REVERSE: sums in decreasing index order; LU_REVERSE: the
 # index-reversed Newton matrix is factored; ULP: exp, log and cbrt one ulp
-# off; STEP_EXP: the step-size factor through exp and log instead of pow.
+# off; STEP_EXP: the step-size factor through exp and log instead of pow;
+# LU_PERMUTE: the Newton matrix factored in a fixed pseudo-random index order.
 VARIANT_SUM_REVERSE, VARIANT_LU_REVERSE, VARIANT_ULP, VARIANT_STEP_EXP = 1, 2, 4, 8
+VARIANT_LU_PERMUTE = 16
 # the set a parity check measures the oracle's own spread with: each
 # variant alone and all of them at once
-VARIANTS = (VARIANT_SUM_REVERSE, VARIANT_LU_REVERSE, VARIANT_ULP, VARIANT_STEP_EXP, 15)
+VARIANTS = (VARIANT_SUM_REVERSE, VARIANT_LU_REVERSE, VARIANT_ULP, VARIANT_STEP_EXP,
+            VARIANT_LU_PERMUTE, 31)
 
 
 def _opts(t_end, rtol, atol, max_attempts=500000, newton_tol=1e-3,
@@ -312,21 +315,24 @@ def replay(net, Y0, T9, rho, t, k, rtol, atol, ln_mult=None, tol=1e-6,
     return x, E.value
 
 
-def forward_sensitivity(net, T9, rho, t, k, x, ln_mult=None, zeta=0.0):
+def forward_sensitivity(net, T9, rho, t, k, x, ln_mult=None, zeta=0.0, h=None, variant=0):
     """d x_final / d theta [n, P] and d E_final / d theta [P] along a recorded
-    schedule; theta = (ln multipliers [R], x0 [n], T9 if not self-heating)."""
+    schedule; theta = (ln multipliers [R], x0 [n], T9 if not self-heating).
+    h: the step sizes of the record (default t_s - t_{s-1}); variant: the
+    rounding variant bits (see VARIANTS)."""
     net = _net(net)
     lib = _load()
     lm = _f64(ln_mult)
     t = _f64(t)
     k = np.ascontiguousarray(k, dtype=np.int32)
     x = _f64(x)
+    h = _f64(h)
     P = net.R + net.n + (0 if net.self_heating else 1)
     dx = np.empty((net.n, P))
     dE = np.empty(P)
     rc = lib.ora_forward_sensitivity(net.ptr, float(T9), float(rho), float(zeta), _p(lm),
-                                     int(t.shape[0] - 1), _p(t), _p(k), _p(x),
-                                     _p(dx), _p(dE))
+                                     int(t.shape[0] - 1), _p(t), _p(k), _p(x), _p(h),
+                                     int(variant), _p(dx), _p(dE))
     if rc != 0:
         raise RuntimeError("singular Newton matrix in forward sensitivity")
     return dx, dE

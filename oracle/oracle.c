@@ -81,7 +81,9 @@
  * factors the index-reversed Newton matrix (partial pivoting kept); bit 4
  * moves every exp, log and cbrt result by one ulp, up or down by the last
  * bit of the argument (another libm of the same accuracy); bit 8 computes the
- * step-size factor 0.9 E^(-1/(q+1)) as 0.9 exp(-ln(E)/(q+1)).  They change no
+ * step-size factor 0.9 E^(-1/(q+1)) as 0.9 exp(-ln(E)/(q+1)); bit 16 factors
+ * the Newton matrix with its indices in a fixed pseudo-random order (another
+ * elimination order; partial pivoting kept).  They change no
  * rule of the method, only the order and the last bits of its floating-point
  * operations.
  *
@@ -136,7 +138,8 @@ typedef struct {
     int32_t variant;            /* rounding variant bits (header), 0 = none */
 } ora_options;
 
-enum { VAR_SUM_REVERSE = 1, VAR_LU_REVERSE = 2, VAR_ULP = 4, VAR_STEP_EXP = 8 };
+enum { VAR_SUM_REVERSE = 1, VAR_LU_REVERSE = 2, VAR_ULP = 4, VAR_STEP_EXP = 8,
+       VAR_LU_PERMUTE = 16 };
 
 /* the rounding variant of the zone this thread is burning (0 outside a burn) */
 static _Thread_local int g_variant = 0;
@@ -458,8 +461,47 @@ static void reverse_vector(double* b, int n) {
     }
 }
 
+/* the fixed pseudo-random order of the permuted-LU variant: position i holds
+   index perm_index(i, n) (multiplication by an odd constant modulo n, a
+   bijection for n not sharing its factors) */
+static int perm_mult(int n) {
+    int m = 7919 % n;
+    for (;; ++m) {
+        int a = m, b = n;
+        while (b) { int t = a % b; a = b; b = t; }
+        if (a == 1 && m > 1) return m;
+        if (m > 4 * n + 8) return 1;
+    }
+}
+
+static void permute_matrix(double* A, int n, int inverse) {
+    int m = perm_mult(n);
+    double* B = malloc(sizeof(double) * n * n);
+    memcpy(B, A, sizeof(double) * n * n);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            int pi = (int)((long)i * m % n), pj = (int)((long)j * m % n);
+            if (inverse) A[pi * n + pj] = B[i * n + j];
+            else A[i * n + j] = B[pi * n + pj];
+        }
+    free(B);
+}
+
+static void permute_vector(double* b, int n, int inverse) {
+    int m = perm_mult(n);
+    double* c = malloc(sizeof(double) * n);
+    memcpy(c, b, sizeof(double) * n);
+    for (int i = 0; i < n; ++i) {
+        int pi = (int)((long)i * m % n);
+        if (inverse) b[pi] = c[i];
+        else b[i] = c[pi];
+    }
+    free(c);
+}
+
 /* factor A (n x n, row-major) in place; returns 0 or -1 if singular */
 static int lu_factor(double* A, int* piv, int n) {
+    if (g_variant & VAR_LU_PERMUTE) permute_matrix(A, n, 0);
     if (g_variant & VAR_LU_REVERSE) reverse_matrix(A, n);
     for (int c = 0; c < n; ++c) {
         int p = c;
@@ -482,6 +524,7 @@ static int lu_factor(double* A, int* piv, int n) {
 }
 
 static void lu_solve(const double* A, const int* piv, int n, double* b) {
+    if (g_variant & VAR_LU_PERMUTE) permute_vector(b, n, 0);
     if (g_variant & VAR_LU_REVERSE) reverse_vector(b, n);
     for (int c = 0; c < n; ++c) {
         int p = piv[c];
@@ -498,6 +541,7 @@ static void lu_solve(const double* A, const int* piv, int n, double* b) {
         b[i] = s / A[i * n + i];
     }
     if (g_variant & VAR_LU_REVERSE) reverse_vector(b, n);
+    if (g_variant & VAR_LU_PERMUTE) permute_vector(b, n, 1);
 }
 
 /* ------------------------------------------------------------------ */
@@ -1032,11 +1076,15 @@ int ora_replay(const ora_network* net, const ora_options* opt, const double* Y0,
 /* Forward sensitivity of the final state and energy along a recorded
    schedule.  Parameters theta, in this order: the R ln-multipliers, the n
    initial-state entries, and (fixed temperature only) T9.  Outputs
-   dx [n * P] (row i, column theta) and dE [P], P = R + n + (1 - self_heating). */
+   dx [n * P] (row i, column theta) and dE [P], P = R + n + (1 - self_heating).
+   tape_h [S+1] or NULL: the step sizes the recorded burn used (else
+   t_s - t_{s-1}, which can differ from them in the last bit).  variant:
+   rounding variant bits, as in ora_options. */
 int ora_forward_sensitivity(const ora_network* net, double T9_fixed, double rho,
                             double zeta, const double* ln_mult, int32_t S, const double* tape_t,
-                            const int32_t* tape_k, const double* tape_x,
-                            double* dx_out, double* dE_out) {
+                            const int32_t* tape_k, const double* tape_x, const double* tape_h,
+                            int32_t variant, double* dx_out, double* dE_out) {
+    g_variant = variant;
     const int N = net->N, R = net->R, n = state_dim(net);
     const int P = R + n + (net->self_heating ? 0 : 1);
     work_t* W = work_alloc(net);
@@ -1054,7 +1102,7 @@ int ora_forward_sensitivity(const ora_network* net, double T9_fixed, double rho,
     for (int i = 0; i < n; ++i) Sh[(size_t)i * P + R + i] = 1.0;  /* ds/dx0 = I */
     for (int s = 1; s <= S; ++s) {
         int kk = tape_k[s];
-        double t_new = tape_t[s], h = t_new - th[0];
+        double t_new = tape_t[s], h = tape_h ? tape_h[s] : t_new - th[0];
         double alpha[KMAX + 1];
         ora_bdf_alpha(kk, t_new, th, h, alpha);
         const double* x = tape_x + (size_t)s * n;
@@ -1138,6 +1186,7 @@ int ora_forward_sensitivity(const ora_network* net, double T9_fixed, double rho,
     }
     memcpy(dx_out, Sh, sizeof(double) * n * P);
     memcpy(dE_out, SEh, sizeof(double) * P);
+    g_variant = 0;
     free(Sh); free(SEh); free(rhs); free(col); free(dedx);
     work_free(W);
     return rc;

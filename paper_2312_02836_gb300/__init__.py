@@ -362,16 +362,19 @@ def burn_host(net: Network, Y0, T9, rho, t_end, rtol, atol, ln_mult=None, *,
 
 
 class Tape:
-    """Device record of a burn's accepted steps, for ``adjoint``."""
+    """Device record of a burn's accepted steps, for ``adjoint``: the schedule
+    of every step and the states at checkpoints every ``ckpt_stride`` steps
+    (0: the library default; 1: every state)."""
 
-    def __init__(self, net: Network, Z: int, max_steps: int):
+    def __init__(self, net: Network, Z: int, max_steps: int, ckpt_stride: int = 0):
         _torch()
         self.net = net
         self.Z = int(Z)
         self.max_steps = int(max_steps)
+        self.ckpt_stride = int(ckpt_stride)
         h = C.c_void_p()
         _abi.check(_abi.load().nb_tape_alloc(net.handle, self.Z, self.max_steps,
-                                             C.byref(h)), "nb_tape_alloc")
+                                             self.ckpt_stride, C.byref(h)), "nb_tape_alloc")
         self._h = h
         self.recorded = None
 
@@ -380,6 +383,25 @@ class Tape:
         if self._h is None:
             raise NetburnError("tape was freed")
         return self._h
+
+    def read(self, z: int) -> dict:
+        """Zone z's record (``nb_tape_read``): numpy arrays t, h, k (order)
+        and x [S+1, n], E [S+1] (NaN where the tape keeps no state), record 0
+        the initial point."""
+        cap = self.max_steps + 1
+        n = self.net.n
+        t = np.empty(cap)
+        h = np.empty(cap)
+        k = np.empty(cap, np.int32)
+        x = np.empty((cap, n))
+        E = np.empty(cap)
+        cnt = C.c_int32(0)
+        _abi.check(_abi.load().nb_tape_read(self.handle, int(z), cap, t.ctypes.data,
+                                            h.ctypes.data, k.ctypes.data, x.ctypes.data,
+                                            E.ctypes.data, C.byref(cnt)), "nb_tape_read")
+        c = cnt.value
+        return dict(t=t[:c].copy(), h=h[:c].copy(), k=k[:c].copy(), x=x[:c].copy(),
+                    E=E[:c].copy())
 
     def _recorded(self, Z, ln_mult, t_end, rtol, atol):
         self.recorded = dict(Z=Z, per_zone=(ln_mult is not None and ln_mult.dim() == 2),

@@ -24,7 +24,7 @@ KERNEL_PLAIN = 1
 # every symbol declared in include/netburn.h
 EXPORTS = ("nb_net_load", "nb_net_free", "nb_net_get_info", "nb_default_options",
            "nb_burn_batch", "nb_burn_batch_host", "nb_tape_alloc", "nb_tape_free",
-           "nb_tape_steps", "nb_burn_adjoint", "nb_burn_batch_noalloc",
+           "nb_tape_steps", "nb_tape_read", "nb_burn_adjoint", "nb_burn_batch_noalloc",
            "nb_burn_multi", "nb_net_specialize", "nb_specialize_source",
            "nb_specialize_compile",
            "nb_exp_eval", "nb_strerror")
@@ -94,7 +94,8 @@ def load(build_if_needed: bool = True):
                                       P, P, P, P, P]
         lib.nb_burn_batch_host.argtypes = [P, I64, P, P, P, D, D, D, P, I32, P,
                                            P, P, P, P, P, P]
-        lib.nb_tape_alloc.argtypes = [P, I64, I32, P]
+        lib.nb_tape_alloc.argtypes = [P, I64, I32, I32, P]
+        lib.nb_tape_read.argtypes = [P, I64, I32, P, P, P, P, P, P]
         lib.nb_tape_free.argtypes = [P]
         lib.nb_tape_steps.argtypes = [P, P]
         lib.nb_burn_adjoint.argtypes = [P, P, I32, P, P, P, P, P, P, P]
@@ -115,7 +116,7 @@ def load(build_if_needed: bool = True):
         lib.nb_strerror.restype = C.c_char_p
         for name in ("nb_net_load", "nb_net_free", "nb_net_get_info",
                      "nb_burn_batch", "nb_burn_batch_host", "nb_tape_alloc",
-                     "nb_tape_free", "nb_tape_steps", "nb_burn_adjoint"):
+                     "nb_tape_free", "nb_tape_steps", "nb_tape_read", "nb_burn_adjoint"):
             getattr(lib, name).restype = C.c_int
         _lib = lib
         return lib

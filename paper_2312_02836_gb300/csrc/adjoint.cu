@@ -14,6 +14,10 @@
 //     dL/dp_r += R_r(x_s) (h c_r^T mu + e_s h / alpha_0 Q_r)
 // (plus mu_T Q_r / c_v in c_r^T mu under self-heating, and the temperature
 // derivative through g_r = d ln lambda_r / dT9 when T9 is a parameter).
+// The tape keeps states only at checkpoints: the reverse sweep takes the steps
+// in blocks of the tape's stride, last block first, recomputes each block's
+// states forward from its checkpointed history window with the forward's
+// own step computation (attempt_solve, so the same bits), then reverses it.
 // One lane per zone, K cotangent sets share each LU factorisation.
 #include <cuda_runtime.h>
 #include <cub/device/device_radix_sort.cuh>
@@ -22,6 +26,7 @@
 #include <cstring>
 
 #include "blob.h"
+#include "adjoint.cuh"
 #include "device.cuh"
 #include "host.h"
 #include "../../include/netburn.h"
@@ -29,173 +34,6 @@
 using namespace nb;
 
 namespace {
-
-struct AdjParams {
-  const unsigned char* blob;
-  int blob_bytes, blob_in_smem;
-  long long Z;
-  int K;
-  TapeDev tape;
-  const double* lnm;
-  int lnm_per_zone;
-  const double *gY, *gE, *gT9;
-  double *dl, *dY0, *dT0;
-  double* ws;
-  long long lane_doubles;  // adjoint workspace per lane
-  int o_lam, o_ee, o_gr, o_gt, o_mu, o_de;
-  unsigned long long* queue;
-  const int32_t* order;    // claim order (zone per claim), longest first, or null
-};
-
-struct AdjZone {
-  long long z;
-  int s;        // next step to reverse
-  bool sh_dummy;
-  Zone fz;      // rates context (rho, lnm)
-};
-
-__device__ __forceinline__ int ring(int s) { return s % HMAX; }
-
-__device__ __forceinline__ const double* rec_ptr(const Net& t, const AdjParams& A,
-                                                 long long z, int s) {
-  return A.tape.rec + ((size_t)z * A.tape.cap + s) * (t.n + 3);
-}
-
-struct AWS {
-  LV lam, ee, gr, gt, mu, de;
-};
-
-__device__ __forceinline__ AWS make_aws(const AdjParams& A, double* lane_base) {
-  AWS a;
-  a.lam.p = lane_base + (size_t)A.o_lam * WS_LANES;
-  a.ee.p = lane_base + (size_t)A.o_ee * WS_LANES;
-  a.gr.p = lane_base + (size_t)A.o_gr * WS_LANES;
-  a.gt.p = lane_base + (size_t)A.o_gt * WS_LANES;
-  a.mu.p = lane_base + (size_t)A.o_mu * WS_LANES;
-  a.de.p = lane_base + (size_t)A.o_de * WS_LANES;
-  return a;
-}
-
-// returns true when the zone needs no reverse steps
-__device__ bool adj_init(const Net& t, AdjZone& Zs, const WS& w, const AWS& a,
-                         const AdjParams& A) {
-  const long long z = Zs.z;
-  const int n = t.n, N = t.N, K = A.K;
-  const int st = A.tape.zstat[z];
-  const int S = A.tape.steps[z] - 1;
-  for (int e = 0; e < HMAX * K * n; ++e) a.lam[e] = 0.0;
-  for (int e = 0; e < HMAX * K; ++e) a.ee[e] = 0.0;
-  for (int e = 0; e < K * t.R; ++e) a.gr[e] = 0.0;
-  for (int q = 0; q < K; ++q) a.gt[q] = 0.0;
-  Zs.s = (st == NB_Z_OK && S >= 0) ? S : -1;
-  if (Zs.s < 0) return true;
-  const int sl = ring(S);
-  for (int q = 0; q < K; ++q) {
-    const size_t qz = (size_t)q * A.Z + z;
-    for (int i = 0; i < N; ++i) a.lam[(sl * K + q) * n + i] = A.gY[qz * N + i];
-    if (t.sh) a.lam[(sl * K + q) * n + N] = A.gT9 ? A.gT9[qz] : 0.0;
-    a.ee[sl * K + q] = A.gE ? A.gE[qz] : 0.0;
-  }
-  Zone& s = Zs.fz;
-  s.z = z;
-  s.rho = A.tape.rho[z];
-  s.rho2 = s.rho * s.rho;
-  s.T9f = A.tape.T9f[z];
-  s.scr = A.tape.scr[z];
-  tab_zone(t, s, rec_ptr(t, A, z, 0) + 2);   // the recorded initial state
-  s.lnm = A.lnm ? (A.lnm_per_zone ? A.lnm + (size_t)z * t.R : A.lnm) : nullptr;
-  if (!t.sh) eval_rates(t, s, w, t_powers(s.T9f, true, s.scr), s.T9f, true);
-  return S == 0;
-}
-
-// reverse one step; returns true when the zone is done
-__device__ bool adj_step(const Net& t, AdjZone& Zs, const WS& w, const AWS& a,
-                         const AdjParams& A) {
-  const long long z = Zs.z;
-  const int n = t.n, N = t.N, K = A.K, s = Zs.s;
-  const double* rs = rec_ptr(t, A, z, s);
-  const int kk = A.tape.ord[(size_t)z * A.tape.cap + s];
-  const double h = rs[1];
-  double tau[KMAX + 1];
-  tau[0] = rs[0];
-#pragma unroll
-  for (int j = 1; j <= KMAX; ++j) tau[j] = (j <= kk) ? rec_ptr(t, A, z, s - j)[0] : 0.0;
-  double alpha[KMAX + 1];
-  bdf_alpha(kk, tau, h, alpha);
-  for (int i = 0; i < n; ++i) w.x[i] = rs[2 + i];
-  if (t.sh) eval_rates(t, Zs.fz, w, t_powers(w.x[N], true, Zs.fz.scr), w.x[N], true);
-  eval_terms(t, w, w.x);
-  assemble_M(t, w, w.x, alpha[0], h);
-  factor_M(t, w);
-  double icv = 0.0;
-  if (t.sh) icv = 1.0 / heat_capacity(t, w.x);
-  if (t.hasE) {
-    for (int i = 0; i < n; ++i) a.de[i] = 0.0;
-    for (int d = 0; d < t.nd; ++d) a.de[t.dt_j[d]] += t.Q[t.dt_r[d]] * w.dt[d];
-    if (t.sh) {
-      double acc = 0.0;
-      for (int r = 0; r < t.R; ++r) acc = fma(t.Q[r], w.dt[t.nd + r], acc);
-      a.de[N] = acc;
-    }
-  }
-  const double ia0 = 1.0 / alpha[0];
-  const int sl = ring(s);
-  int sj[KMAX + 1];
-#pragma unroll
-  for (int j = 1; j <= KMAX; ++j) sj[j] = ring(s + HMAX - j);
-  for (int q = 0; q < K; ++q) {
-    const int lo = (sl * K + q) * n;
-    const double es = a.ee[sl * K + q];
-    const double ce = es * h * ia0;
-    for (int i = 0; i < n; ++i) {
-      double v = a.lam[lo + i];
-      if (t.hasE) v = fma(ce, a.de[i], v);
-      a.mu[i] = v;
-      a.lam[lo + i] = 0.0;
-    }
-    a.ee[sl * K + q] = 0.0;
-    tri_solve(t.tfw, t.tfw_s, t.tfw_c, n, w.lu, a.mu);
-    tri_solve(t.tbw, t.tbw_s, t.tbw_c, n, w.lu, a.mu);
-#pragma unroll
-    for (int j = 1; j <= KMAX; ++j) {
-      if (j > kk) continue;
-      const int lj = (sj[j] * K + q) * n;
-      const double ma = -alpha[j];
-      for (int i = 0; i < n; ++i) a.lam[lj + i] = fma(ma, a.mu[i], a.lam[lj + i]);
-      if (t.hasE) a.ee[sj[j] * K + q] = fma(-es * ia0, alpha[j], a.ee[sj[j] * K + q]);
-    }
-    const double muT = t.sh ? a.mu[N] * icv : 0.0;
-    double gt = 0.0;
-    for (int r = 0; r < t.R; ++r) {
-      double acc = 0.0;
-      for (int e = t.rg_ptr[r]; e < t.rg_ptr[r + 1]; ++e)
-        acc = fma(t.rg_c[e], a.mu[t.rg_i[e]], acc);
-      const double Qr = t.Q[r];
-      acc = fma(muT, Qr, acc);
-      const double v = w.rr[r] * fma(h, acc, ce * Qr);
-      a.gr[q * t.R + r] += v;
-      if (!t.sh) gt = fma(v, w.g[r], gt);
-    }
-    a.gt[q] += gt;
-  }
-  Zs.s = s - 1;
-  return Zs.s == 0;
-}
-
-__device__ void adj_finish(const Net& t, const AdjZone& Zs, const AWS& a,
-                           const AdjParams& A) {
-  const long long z = Zs.z;
-  const int n = t.n, N = t.N, K = A.K;
-  const bool ok = Zs.s == 0;
-  const int s0 = ring(0);
-  for (int q = 0; q < K; ++q) {
-    const size_t qz = (size_t)q * A.Z + z;
-    for (int r = 0; r < t.R; ++r) A.dl[qz * t.R + r] = ok ? a.gr[q * t.R + r] : 0.0;
-    if (A.dY0)
-      for (int i = 0; i < N; ++i) A.dY0[qz * N + i] = ok ? a.lam[(s0 * K + q) * n + i] : 0.0;
-    if (A.dT0) A.dT0[qz] = ok ? (t.sh ? a.lam[(s0 * K + q) * n + N] : a.gt[q]) : 0.0;
-  }
-}
 
 __global__ void __launch_bounds__(128) k_adjoint(AdjParams A) {
   extern __shared__ __align__(16) unsigned char sm[];
@@ -216,6 +54,10 @@ __global__ void __launch_bounds__(128) k_adjoint(AdjParams A) {
   AdjZone Zs;
   Zs.z = -1;
   Zs.s = -1;
+  Zs.rs = 1;
+  Zs.re = 0;
+  Zs.lo = 1;
+  Zs.fail = false;
   bool active = false, retired = false, fresh = false;
   for (;;) {
     const unsigned need = __ballot_sync(0xffffffffu, !active && !retired);
@@ -241,6 +83,8 @@ __global__ void __launch_bounds__(128) k_adjoint(AdjParams A) {
       if (fresh) {
         done = adj_init(t, Zs, w, a, A);
         fresh = false;
+      } else if (Zs.rs <= Zs.re) {
+        done = adj_replay(t, Zs, w, a, A);
       } else {
         done = adj_step(t, Zs, w, a, A);
       }
@@ -275,6 +119,8 @@ extern "C" int nb_burn_adjoint(nb_net net, void* tape, int32_t K, const double* 
   A.Z = Z;
   A.K = K;
   A.tape = tp->dev;
+  A.rtol = tp->rtol;
+  A.atol = tp->atol;
   A.lnm = tp->has_lnm ? tp->lnm : nullptr;
   A.lnm_per_zone = tp->lnm_per_zone;
   A.gY = gY; A.gE = gE; A.gT9 = gT9;
@@ -287,6 +133,7 @@ extern "C" int nb_burn_adjoint(nb_net net, void* tape, int32_t K, const double* 
   A.o_gt = (int)off; off += K;
   A.o_mu = (int)off; off += n;
   A.o_de = (int)off; off += n;
+  A.o_seg = (int)off; off += (long long)tp->dev.stride * n;
   A.lane_doubles = off;
   // one zone per lane; smaller blocks when there are few zones per SM
   const long long per_sm = (Z + net->sm_count - 1) / net->sm_count;

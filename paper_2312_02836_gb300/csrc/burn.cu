@@ -569,19 +569,28 @@ extern "C" int nb_burn_batch_host(nb_net net, int64_t Z, const double* Y0,
 
 // ------------------------------------------------------------------ tape
 
-extern "C" int nb_tape_alloc(nb_net net, int64_t Z, int32_t max_steps, void** tape) {
-  if (!net || !tape || Z <= 0 || max_steps < 1) return NB_E_ARG;
+extern "C" int nb_tape_alloc(nb_net net, int64_t Z, int32_t max_steps, int32_t ckpt_stride,
+                             void** tape) {
+  if (!net || !tape || Z <= 0 || max_steps < 1 || max_steps > 0x3ffffffe || ckpt_stride < 0)
+    return NB_E_ARG;
   *tape = nullptr;
   nb_tape_s* tp = new (std::nothrow) nb_tape_s();
   if (!tp) return NB_E_NOMEM;
   tp->net = net;
   tp->Z = Z;
   tp->cap = max_steps + 1;
+  tp->dev.stride = ckpt_stride > 0 ? ckpt_stride : NB_TAPE_DEFAULT_STRIDE;
+  const int m = std::min(tp->dev.stride, HMAX);
+  const long long blocks = (max_steps + tp->dev.stride - 1) / tp->dev.stride;
+  if (1 + blocks * m > 0x7fffffffLL) { delete tp; return NB_E_ARG; }
+  tp->dev.scap = (int32_t)(1 + blocks * m);
   const int n = net->h.n;
-  const size_t rec = (size_t)Z * tp->cap * (n + 3) * sizeof(double);
+  const size_t sched = (size_t)Z * tp->cap * 2 * sizeof(double);
   const size_t ord = (size_t)Z * tp->cap;
-  bool ok = cudaMalloc(&tp->dev.rec, rec) == cudaSuccess &&
+  const size_t states = (size_t)Z * tp->dev.scap * (n + 1) * sizeof(double);
+  bool ok = cudaMalloc(&tp->dev.sched, sched) == cudaSuccess &&
             cudaMalloc(&tp->dev.ord, ord) == cudaSuccess &&
+            cudaMalloc(&tp->dev.states, states) == cudaSuccess &&
             cudaMalloc(&tp->dev.steps, (size_t)Z * 4) == cudaSuccess &&
             cudaMalloc(&tp->dev.zstat, (size_t)Z * 4) == cudaSuccess &&
             cudaMalloc(&tp->dev.rho, (size_t)Z * 8) == cudaSuccess &&
@@ -590,10 +599,8 @@ extern "C" int nb_tape_alloc(nb_net net, int64_t Z, int32_t max_steps, void** ta
             cudaMalloc(&tp->lnm, (size_t)Z * std::max(net->h.R, 1) * 8) == cudaSuccess;
   tp->dev.cap = tp->cap;
   if (!ok) {
-    cudaFree(tp->dev.rec); cudaFree(tp->dev.ord); cudaFree(tp->dev.steps);
-    cudaFree(tp->dev.zstat); cudaFree(tp->dev.rho); cudaFree(tp->dev.T9f);
-    cudaFree(tp->dev.scr);
-    cudaFree(tp->lnm);
+    cudaGetLastError();
+    tape_release(tp);
     delete tp;
     return NB_E_NOMEM;
   }
@@ -604,10 +611,7 @@ extern "C" int nb_tape_alloc(nb_net net, int64_t Z, int32_t max_steps, void** ta
 extern "C" int nb_tape_free(void* tape) {
   nb_tape_s* tp = (nb_tape_s*)tape;
   if (!tp || tp->magic != 0x7a9e5eedu) return NB_E_ARG;
-  cudaFree(tp->dev.rec); cudaFree(tp->dev.ord); cudaFree(tp->dev.steps);
-  cudaFree(tp->dev.zstat); cudaFree(tp->dev.rho); cudaFree(tp->dev.T9f);
-    cudaFree(tp->dev.scr);
-  cudaFree(tp->lnm);
+  tape_release(tp);
   tp->magic = 0;
   delete tp;
   return NB_OK;
@@ -620,3 +624,39 @@ extern "C" int nb_tape_steps(void* tape, const int32_t** steps) {
   return NB_OK;
 }
 
+extern "C" int nb_tape_read(void* tape, int64_t z, int32_t cap, double* t, double* h,
+                            int32_t* order, double* x, double* E, int32_t* count) {
+  nb_tape_s* tp = (nb_tape_s*)tape;
+  if (!tp || tp->magic != 0x7a9e5eedu || !count || cap < 0) return NB_E_ARG;
+  if (!tp->recorded) return NB_E_TAPE;
+  if (z < 0 || z >= tp->recZ) return NB_E_ARG;
+  const int n = tp->net->h.n;
+  std::lock_guard<std::mutex> lk(tp->net->mu);
+  CK(cudaDeviceSynchronize());
+  int32_t cnt = 0;
+  CK(cudaMemcpy(&cnt, tp->dev.steps + z, 4, cudaMemcpyDeviceToHost));
+  *count = cnt;
+  if (cnt > cap) return NB_E_ARG;
+  if (cnt == 0) return NB_OK;
+  std::vector<double> sched((size_t)cnt * 2);
+  std::vector<int8_t> ord(cnt);
+  CK(cudaMemcpy(sched.data(), tp->dev.sched + (size_t)z * tp->cap * 2, sched.size() * 8,
+                cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(ord.data(), tp->dev.ord + (size_t)z * tp->cap, cnt, cudaMemcpyDeviceToHost));
+  int kept = 0;   // state slots in use: they increase with the record index
+  for (int q = 0; q < cnt; ++q) kept = std::max(kept, tape_state_slot(q, tp->dev.stride) + 1);
+  std::vector<double> st((size_t)kept * (n + 1));
+  if (kept)
+    CK(cudaMemcpy(st.data(), tp->dev.states + (size_t)z * tp->dev.scap * (n + 1),
+                  st.size() * 8, cudaMemcpyDeviceToHost));
+  for (int q = 0; q < cnt; ++q) {
+    if (t) t[q] = sched[2 * q];
+    if (h) h[q] = sched[2 * q + 1];
+    if (order) order[q] = ord[q];
+    const int slot = tape_state_slot(q, tp->dev.stride);
+    for (int i = 0; i < n; ++i)
+      if (x) x[(size_t)q * n + i] = slot >= 0 ? st[(size_t)slot * (n + 1) + i] : NAN;
+    if (E) E[q] = slot >= 0 ? st[(size_t)slot * (n + 1) + n] : NAN;
+  }
+  return NB_OK;
+}

@@ -45,7 +45,7 @@ struct nb_tape_s {
   nb_net net;
   long long Z;
   int cap;
-  nb::TapeDev dev;
+  nb::TapeDev dev{};
   long long recZ = 0;       // zones of the recorded burn
   double* lnm = nullptr;   // copy of the multipliers of the recorded burn
   int lnm_per_zone = 0;
@@ -54,6 +54,13 @@ struct nb_tape_s {
   int recorded = 0;
   unsigned magic = 0x7a9e5eedu;
 };
+
+// device buffers of a tape (each may be null)
+inline void tape_release(nb_tape_s* tp) {
+  cudaFree(tp->dev.sched); cudaFree(tp->dev.ord); cudaFree(tp->dev.states);
+  cudaFree(tp->dev.steps); cudaFree(tp->dev.zstat); cudaFree(tp->dev.rho);
+  cudaFree(tp->dev.T9f); cudaFree(tp->dev.scr); cudaFree(tp->lnm);
+}
 
 #define CK(call)                                                   \
   do {                                                             \

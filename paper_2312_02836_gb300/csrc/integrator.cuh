@@ -57,17 +57,32 @@ struct LV {
   }
 };
 
-// Tape written by a burn that will be differentiated.
+// Tape written by a burn that will be differentiated: the schedule of every
+// accepted step, and the states only at checkpoints.  Record s = 0 is the
+// initial point, record s >= 1 accepted step s.  A state is kept for s = 0
+// and for the last min(stride, HMAX) steps of every block of `stride` steps,
+// which is the history window the reverse sweep restarts a segment from
+// (tape_state_slot); stride 1 keeps every state.
 struct TapeDev {
-  double* rec;       // [Z, cap, n + 3]: t, h, x[0..n), E
-  int8_t* ord;       // [Z, cap] BDF order of the step (0 for the start point)
-  int32_t* steps;    // [Z] records written
+  double* sched;     // [Z, cap, 2]: t_s, h_s (the step size the forward used)
+  int8_t* ord;       // [Z, cap] BDF order of step s (0 for s = 0)
+  double* states;    // [Z, scap, n + 1]: x_s, E_s of the kept records
+  int32_t* steps;    // [Z] records written (accepted steps + 1)
   int32_t* zstat;    // [Z] status the zone finished with
   double* rho;       // [Z]
   double* T9f;       // [Z] fixed temperature (or initial T9)
   double* scr;       // [Z] screening factor sqrt(rho zeta) 10^-4.5 of the zone
-  int32_t cap;
+  int32_t cap, scap, stride;
 };
+
+// slot of record s's state on the tape, or -1 when it is not kept (host
+// code reads tapes too)
+__host__ __device__ __forceinline__ int tape_state_slot(int s, int stride) {
+  if (s == 0) return 0;
+  const int m = stride < HMAX ? stride : HMAX;
+  const int b = (s - 1) / stride, p = (s - 1) - b * stride;
+  return p >= stride - m ? 1 + b * m + (p - (stride - m)) : -1;
+}
 
 struct BurnParams {
   const unsigned char* blob;
@@ -456,8 +471,8 @@ NB_HD __forceinline__ double order_estimate(const NT& t, const Zone& s, WT& w, i
   return acc * t.inv_n;   // E_q^2
 }
 
-// Record an accepted point (time, step, state, energy, order); false when
-// the zone's tape is full.
+// Record an accepted point (time, step, order; state and energy when the
+// record is a kept one); false when the zone's tape is full.
 template <class NT, class V>
 NB_HD __forceinline__ bool tape_record(const NT& t, const BurnParams& P, const Zone& s,
                                        const V& x, double h, int ord) {
@@ -465,13 +480,17 @@ NB_HD __forceinline__ bool tape_record(const NT& t, const BurnParams& P, const Z
   int32_t* cnt = P.tape.steps + s.z;
   const int idx = *cnt;
   if (idx >= P.tape.cap) return false;
-  double* rec = P.tape.rec + ((unsigned long long)s.z * P.tape.cap + idx) * (t.n + 3);
-  rec[0] = s.t;
-  rec[1] = h;
-  NB_UNROLL
-  for (int i = 0; i < t.n; ++i) rec[2 + i] = x[i];
-  rec[2 + t.n] = s.E;
-  P.tape.ord[(unsigned long long)s.z * P.tape.cap + idx] = (int8_t)ord;
+  const unsigned long long r = (unsigned long long)s.z * P.tape.cap + idx;
+  P.tape.sched[2 * r] = s.t;
+  P.tape.sched[2 * r + 1] = h;
+  P.tape.ord[r] = (int8_t)ord;
+  const int slot = tape_state_slot(idx, P.tape.stride);
+  if (slot >= 0) {
+    double* rec = P.tape.states + ((unsigned long long)s.z * P.tape.scap + slot) * (t.n + 1);
+    NB_UNROLL
+    for (int i = 0; i < t.n; ++i) rec[i] = x[i];
+    rec[t.n] = s.E;
+  }
   *cnt = idx + 1;
   return true;
 }
@@ -591,30 +610,24 @@ NB_HD __forceinline__ bool zone_init(const NT& t, Zone& s, WT& w, const BurnPara
 
 // ---------------------------------------------------------------- one attempt
 
-// One step attempt.  Returns true when the zone is finished.
+// The computation of one step attempt from t_n = s.t to t_new with step h at
+// order kk: BDF coefficients, history sum, weights from x_n, predictor,
+// Jacobian and LU at the predictor, modified Newton.  Leaves the solution in
+// w.x and the predictor in w.xp, alpha_0..alpha_kk in alpha and, with
+// self-heating, the reference temperature of the rates in Tref (powers
+// pref); returns true when Newton converged.  The forward burn and the
+// adjoint's recomputation of checkpointed segments both run it, so that they
+// produce the same bits.
 template <class NT, class WT>
-NB_HD __forceinline__ bool zone_attempt(const NT& t, Zone& s, WT& w, const BurnParams& P) {
+NB_HD __forceinline__ bool attempt_solve(const NT& t, Zone& s, WT& w, double atol, double rtol,
+                                         double h, double t_new, int kk, double* alpha,
+                                         TPow& pref, double& Tref) {
   const int n = t.n, N = t.N;
-  if (s.c_acc + s.c_rej_err + s.c_rej_newton >= P.max_attempts) {
-    s.status = NB_Z_MAX_STEPS;
-    return true;
-  }
-  double h = s.h;
-  if (h < 1e-30 * s.tend || h < 1e-14 * s.t) {
-    s.status = NB_Z_DT_UNDERFLOW;
-    return true;
-  }
-  double t_new;
-  if (s.t + h >= s.tend) { h = s.tend - s.t; t_new = s.tend; }
-  else t_new = s.t + h;
-  const int kk = s.k < s.nh ? s.k : s.nh;
-
   // alpha_j = h l_j'(t_new) over t_new, t_n, .., t_{n+1-kk}
   double tau[KMAX + 1];
   tau[0] = t_new;
 #pragma unroll 1
   for (int j = 1; j <= kk; ++j) tau[j] = w.th[hslot(s, j - 1)];
-  double alpha[KMAX + 1];
   bdf_alpha(kk, tau, h, alpha);
   // psi = sum_{j>=1} alpha_j x_{n+1-j}; weights from x_n
   {
@@ -624,7 +637,7 @@ NB_HD __forceinline__ bool zone_attempt(const NT& t, Zone& s, WT& w, const BurnP
     hist_combine(t, w, kk, alpha + 1, base, w.psi);
     const int b0 = hslot(s, 0) * n;
     NB_UNROLL
-    for (int i = 0; i < n; ++i) w.iw[i] = 1.0 / (P.atol + P.rtol * fabs(w.xh[b0 + i]));
+    for (int i = 0; i < n; ++i) w.iw[i] = 1.0 / (atol + rtol * fabs(w.xh[b0 + i]));
   }
   // predictor
   if (s.nh >= kk + 1) extrapolate(t, s, w, 0, kk, t_new, w.xp);
@@ -638,8 +651,7 @@ NB_HD __forceinline__ bool zone_attempt(const NT& t, Zone& s, WT& w, const BurnP
   for (int i = 0; i < n; ++i) w.x[i] = w.xp[i];
   // Jacobian at the predictor, M, LU; with self-heating the predictor's
   // temperature is the attempt's reference for the rates
-  TPow pref;
-  double Tref = 0.0;
+  Tref = 0.0;
   if (t.sh) {
     Tref = w.x[N];
     pref = t_powers(Tref, true, s.scr);
@@ -678,6 +690,30 @@ NB_HD __forceinline__ bool zone_attempt(const NT& t, Zone& s, WT& w, const BurnP
     }
     nrm_prev = nrm2;
   }
+  return converged;
+}
+
+// One step attempt.  Returns true when the zone is finished.
+template <class NT, class WT>
+NB_HD __forceinline__ bool zone_attempt(const NT& t, Zone& s, WT& w, const BurnParams& P) {
+  const int n = t.n, N = t.N;
+  if (s.c_acc + s.c_rej_err + s.c_rej_newton >= P.max_attempts) {
+    s.status = NB_Z_MAX_STEPS;
+    return true;
+  }
+  double h = s.h;
+  if (h < 1e-30 * s.tend || h < 1e-14 * s.t) {
+    s.status = NB_Z_DT_UNDERFLOW;
+    return true;
+  }
+  double t_new;
+  if (s.t + h >= s.tend) { h = s.tend - s.t; t_new = s.tend; }
+  else t_new = s.t + h;
+  const int kk = s.k < s.nh ? s.k : s.nh;
+  double alpha[KMAX + 1];
+  TPow pref;
+  double Tref;
+  const bool converged = attempt_solve(t, s, w, P.atol, P.rtol, h, t_new, kk, alpha, pref, Tref);
   if (!converged) {
     s.c_rej_newton++;
     if (++s.nfail >= 10) { s.status = NB_Z_NEWTON_FAIL; return true; }
@@ -757,6 +793,28 @@ NB_HD __forceinline__ bool zone_attempt(const NT& t, Zone& s, WT& w, const BurnP
   if (factor >= 1.0 && factor < 1.2) factor = 1.0;
   s.h = h * factor;
   return false;
+}
+
+// Recompute accepted step (h, t_new, order kk) of a recorded burn from the
+// history held in w and push its solution (the adjoint's recomputation of a
+// checkpointed segment; energies are not recomputed).  The forward burn's
+// attempt converged on the same inputs, so this one does too; false if not.
+template <class NT, class WT>
+NB_HD __forceinline__ bool replay_step(const NT& t, Zone& s, WT& w, double atol, double rtol,
+                                       double h, double t_new, int kk) {
+  double alpha[KMAX + 1];
+  TPow pref;
+  double Tref;
+  if (!attempt_solve(t, s, w, atol, rtol, h, t_new, kk, alpha, pref, Tref)) return false;
+  s.hh = s.hh == 0 ? HMAX - 1 : s.hh - 1;
+  const int b0 = s.hh * t.n;
+  NB_UNROLL
+  for (int i = 0; i < t.n; ++i) w.xh[b0 + i] = w.x[i];
+  w.th[s.hh] = t_new;
+  w.eh[s.hh] = 0.0;
+  if (s.nh < HMAX) s.nh++;
+  s.t = t_new;
+  return true;
 }
 
 // GPU global timer (ns)

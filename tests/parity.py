@@ -27,9 +27,11 @@ deviation is within twice that measured noise:
     (at least one).  They are held to twice the variants' spread over all
     zones, diverged ones included;
   * a zone's final status must equal the oracle's, except on zones where a
-    rounding variant's status differs from the oracle's too (an outcome
-    decided by rounding, e.g. a Newton iteration at the FP64 noise floor of
-    its convergence test); such zones are reported and not compared further.
+    rounding variant's status differs from the oracle's too: there the
+    outcome is decided by rounding (measured on the runaway zones of the
+    128-species network, T9 -> 15, rates ~1e80, where the variants end OK,
+    NEWTON_FAIL or DT_UNDERFLOW after 1,000 to 27,000 steps).  Such zones
+    are reported and not compared further, whatever the GPU's status.
 
 The factor 2 is the margin for one more independent rounding realisation
 (the GPU) against the maximum over a handful of them.  Measured spreads
@@ -63,6 +65,8 @@ def oracle_spread(ora: dict, variants, atol: float, rtol: float) -> dict:
               status_sensitive=np.zeros(Yo.shape[0], dtype=bool))
     for v in variants:
         sp["status_sensitive"] |= np.asarray(v["status"]) != np.asarray(ora["status"])
+    ok = ok & ~sp["status_sensitive"]
+    for v in variants:
         dv = np.asarray(v["counters"])[:, 0].astype(np.int64) - acc
         same = ok & (dv == 0) & (np.asarray(v["status"]) == 0)
         both = ok & (np.asarray(v["status"]) == 0)
@@ -101,8 +105,9 @@ def compare(gpu: dict, ora: dict, atol: float, rtol: float = 1e-8, spread: dict 
     bad = np.where((sg != so) & ~sens)[0]
     assert bad.size == 0, f"status differs in zones {bad[:10]}: gpu {sg[bad[:10]]} oracle {so[bad[:10]]}"
     rep["status_differs_rounding_decided"] = [int(z) for z in np.where(sg != so)[0]]
+    rep["rounding_decided_zones"] = [int(z) for z in np.where(sens)[0]]
     rep["oracle_spread"]["status_sensitive_zones"] = int(sens.sum())
-    ok = (so == 0) & (sg == so)
+    ok = (so == 0) & (sg == so) & ~sens
     dacc = cg[:, 0].astype(np.int64) - co[:, 0].astype(np.int64)
     rep["max_step_diff"] = int(np.abs(dacc[ok]).max()) if ok.any() else 0
     lim_steps = max(2, spread["max_step_diff"])

@@ -76,7 +76,7 @@ def test_burn_argument_checks_on_host():
     # a null network handle is rejected before any device work
     assert lib.nb_burn_batch(None, 4, None, None, None, 1.0, 1e-8, 1e-12, None, 0,
                              None, None, None, None, None, None, None, None) == -1
-    assert lib.nb_tape_alloc(None, 4, 10, None) == -1
+    assert lib.nb_tape_alloc(None, 4, 10, 0, None) == -1
 
 
 def test_package_refuses_without_gpu():
