@@ -37,6 +37,21 @@ WORKLOAD_DESC = ("13-species alpha chain with self-heating (12 rates, Q~U[1,10])
                  "t_end 1e-3 s, rtol 1e-8, atol 1e-12")
 
 
+# The other workloads of the configuration table, each a sub-entry of the
+# line (name, zones, options of config_entry): the fixed-temperature chain,
+# the 48-species network at its full 262,144 zones, and the 128-species
+# self-heating network on a seeded prefix of its zones (its full 131,072
+# zones take about 1.8e17 flops, a day and a half at the FP64 peak), with a
+# watchdog.  The sensitivity workload is the "adjoint" entry.
+CONFIG_TABLE = {
+    "cfg0": ("chain13", None, dict(cpu_zones=4096)),
+    "cfg2": ("net48", None, dict(cpu_zones=256)),
+    "cfg4": ("net128_heat", 1024, dict(cpu_zones=16, plain_zones=0, steps=1, warmup=0,
+                                       budget_s=60.0, launch=dict(kernel="coop"),
+                                       full_zones=131072)),
+}
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -48,7 +63,7 @@ def dist_env():
 # exp, the compiled-network layout, the generic network walk and the code
 # generator of the specialised kernel, and the launch code
 KERNEL_SOURCES = ("integrator.cuh", "expf64.cuh", "blob.h", "device.cuh", "netload.cpp",
-                  "codegen.cpp", "burn.cu")
+                  "codegen.cpp", "burn.cu", "coop.cuh", "adjoint.cuh", "adjoint.cu")
 
 
 def kernel_source_hash() -> str:
@@ -70,11 +85,11 @@ def launch_shape(launch, variant):
                       (launch.get("blocks_per_sm", 0) or 1), variant)
 
 
-def profiled_traffic(kernel, Z, shape):
-    """DRAM bytes per launch from the committed ncu summary of this kernel,
-    or None when the kernel sources, the zone count or the launch shape
-    differ from the profiled ones."""
-    path = os.path.join(ROOT, "profiles", kernel + "_chain13_heat.md")
+def profiled_traffic(kernel, Z, shape, workload="chain13_heat"):
+    """DRAM bytes per launch from the committed ncu summary of this kernel on
+    this workload, or None when the kernel sources, the zone count or the
+    launch shape (None: not checked) differ from the profiled ones."""
+    path = os.path.join(ROOT, "profiles", kernel + "_" + workload + ".md")
     if not os.path.exists(path):
         return None
     kv = {}
@@ -83,7 +98,7 @@ def profiled_traffic(kernel, Z, shape):
             k, v = line.split(":", 1)
             kv[k.strip()] = v.strip()
     if (kv.get("source_hash") == kernel_source_hash() and kv.get("zones") == str(Z)
-            and kv.get("launch") == shape and "dram_bytes_per_launch" in kv):
+            and (shape is None or kv.get("launch") == shape) and "dram_bytes_per_launch" in kv):
         return int(kv["dram_bytes_per_launch"])
     return None
 
@@ -130,6 +145,12 @@ class Clocks:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def zone_bytes(N: int) -> int:
+    """Algorithmic HBM bytes per zone-burn: Y0, T9, rho in; Y, T9, E, eight
+    int32 counters and the status out."""
+    return 16 * N + 8 * 4 + 8 * 4 + 4
+
+
 def workload_desc(name: str, Z: int) -> str:
     c = gen.CONFIGS[name]
     net = gen.network(name)
@@ -152,12 +173,18 @@ def sampled_parity(name, net, z, s, out, n) -> dict:
     o = run(0)
     spread = oracle_spread(o, [run(v) for v in oracle.VARIANTS], s["atol"], s["rtol"])
     g = {k: v[sel] for k, v in to_numpy(out).items()}
+    fin = g["status"] != 6          # zones the watchdog stopped are not compared
+    if not fin.all():
+        g = {k: v[fin] for k, v in g.items()}
+        o = {k: (v[fin] if isinstance(v, np.ndarray) else v) for k, v in o.items()}
+        spread = dict(spread, status_sensitive=spread["status_sensitive"][fin])
     try:
         rep = compare(g, o, s["atol"], rtol=s["rtol"], spread=spread)
         rep["passed"] = True
     except AssertionError as e:
         rep = {"passed": False, "error": str(e)[:300]}
     rep["sample"] = int(sel.size)
+    rep["compared_finished"] = int(fin.sum())
     return rep
 
 
@@ -334,7 +361,7 @@ def run_native(args):
                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2070 MHz",
                 "flops_per_launch": ops["flops"],
                 "special_functions_per_launch": ops["special"],
-                "algorithmic_bytes_per_launch": int(Z * (13 * 8 * 2 + 8 * 4 + 8 * 4 + 4))}
+                "algorithmic_bytes_per_launch": int(Z * zone_bytes(net_spec.N))}
 
     base = None
     if not args.no_cpu_baseline:
@@ -348,6 +375,12 @@ def run_native(args):
     if args.adjoint:
         adj = adjoint_bench(nb, torch, dev, flush, metrics)
     multi = multi_bench(nb, torch, dev, flush) if args.multi else None
+    configs = {}
+    for cname in [c for c in args.configs.split(",") if c]:
+        name, Zc, kw = CONFIG_TABLE[cname]
+        sp = min(args.sample_parity, 32) if cname == "cfg4" else args.sample_parity
+        configs[cname] = config_entry(nb, torch, dev, flush, metrics, name, Zc,
+                                      sample_parity=sp, **kw)
 
     line = {"metric": METRIC, "value": value, "unit": "zone-burns/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_ms,
@@ -383,13 +416,122 @@ def run_native(args):
         line["multi_network"] = multi
     if parity is not None:
         line["sampled_parity"] = parity
+    if configs:
+        line["configs"] = configs
     print(json.dumps(line), flush=True)
 
 
-def adjoint_bench(nb, torch, dev, flush, metrics) -> dict:
+def config_entry(nb, torch, dev, flush, metrics, name, Z=None, steps=3, warmup=1,
+                 sample_parity=256, cpu_zones=256, tune_zones=32768, plain_zones=16384,
+                 budget_s=0.0, launch=None, full_zones=None) -> dict:
+    """One workload of the configuration table at its size: zone-burns/s of
+    the autotuned persistent launch (autotuned on the first tune_zones zones,
+    the launch shape does not depend on the zone count once lanes are
+    outnumbered), the FP64 roofline of its kernel, the plain one-thread-per-
+    zone launch on a prefix of plain_zones zones, the oracle on cpu_zones
+    zones of the host, and the launch's sampled parity with the oracle.
+    budget_s > 0: the device watchdog ends zones still burning after that
+    long (the entry then counts only finished zones).  launch: a fixed
+    launch instead of the autotuner's.  full_zones: the workload's full size,
+    when Z is a prefix of it: the entry projects the full burn's time from
+    the prefix's flops and FP64 rate."""
+    from paper_2312_02836_gb300.autotune import autotune
+    net, z, s = gen.problem(name, Z)
+    Z = z["T9"].shape[0]
+    nc = nb.Network(net)
+    info = nc.info()
+    d = {k: torch.from_numpy(v).to(dev) for k, v in z.items()}
+    zk = dict(zeta=d["zeta"]) if "zeta" in d else {}
+    if launch is None:
+        Zt = min(Z, tune_zones)
+        tz = {k: v[:Zt].contiguous() for k, v in d.items()}
+        launch = autotune(nc, tz["Y"], tz["T9"], tz["rho"], s["t_end"], s["rtol"], s["atol"],
+                          extra=dict(zeta=tz["zeta"]) if "zeta" in tz else {},
+                          key=f"{name}:{Zt}")
+        tune_ms = launch.pop("_timings_ms")
+    else:
+        launch, tune_ms = dict(launch), []
+    stream = torch.cuda.current_stream(dev)
+    out = None
+
+    def step(**extra):
+        nonlocal out
+        out = nb.burn(nc, d["Y"], d["T9"], d["rho"], s["t_end"], s["rtol"], s["atol"],
+                      out=out, time_budget_s=budget_s, **{**launch, **extra}, **zk)
+
+    for _ in range(warmup):
+        step()
+    ms = []
+    for k in range(steps):
+        flush.fill_(float(k))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    mean_ms = statistics.mean(ms)
+    counters = out.counters.cpu().numpy()
+    status = out.status.cpu().numpy()
+    done = status != 6
+    ops = metrics.burn_ops(info, counters[done], net.self_heating)
+    achieved = ops["flops"] / (mean_ms * 1e-3) / 1e12
+    kernel = launch.get("kernel", "persistent")
+    kname = {"coop": "k_burn_coop"}.get(kernel, "nb_spec_burn" if nc.info()["last_specialized"]
+                                        else "k_burn_persistent")
+    entry = {"workload": workload_desc(name, Z), "zones": Z,
+             "value": int(done.sum()) / (mean_ms * 1e-3), "unit": "zone-burns/s",
+             "ms_per_step": mean_ms, "steps": steps, "launch": launch,
+             "autotune_ms": [[c, round(m, 2)] for c, m in tune_ms],
+             "zones_ok": int((status == 0).sum()), "zones_timed_out": int((~done).sum()),
+             "roofline": {"bound": "alu", "achieved": achieved,
+                          "peak": metrics.FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                          "frac": achieved / metrics.FP64_PEAK_TFLOPS,
+                          "traffic": profiled_traffic(kname, Z, None, workload=name),
+                          "kernel": kname, "flops_per_launch": ops["flops"],
+                          "algorithmic_bytes_per_launch": int(Z * zone_bytes(net.N)),
+                          "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2070 MHz"},
+             "events": ops["events"]}
+    if budget_s > 0:
+        entry["time_budget_s"] = budget_s
+    if full_zones and done.any():
+        per_zone = ops["flops"] / done.sum()
+        entry["projected_full_size"] = {
+            "zones": full_zones, "flops": per_zone * full_zones,
+            "seconds_at_this_rate": per_zone * full_zones / (achieved * 1e12),
+            "seconds_at_fp64_peak": per_zone * full_zones / (metrics.FP64_PEAK_TFLOPS * 1e12),
+            "basis": f"mean algorithmic flops of the {int(done.sum())} finished zones of a "
+                     f"{Z}-zone seeded prefix"}
+    if plain_zones:
+        Zp = min(Z, plain_zones)
+        pz = {k: v[:Zp].contiguous() for k, v in d.items()}
+        pzk = dict(zeta=pz["zeta"]) if "zeta" in pz else {}
+        nb.burn(nc, pz["Y"], pz["T9"], pz["rho"], s["t_end"], s["rtol"], s["atol"],
+                kernel="plain", time_budget_s=budget_s, **pzk)
+        flush.fill_(5.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        po = nb.burn(nc, pz["Y"], pz["T9"], pz["rho"], s["t_end"], s["rtol"], s["atol"],
+                     kernel="plain", time_budget_s=budget_s, **pzk)
+        b.record(stream)
+        torch.cuda.synchronize()
+        pdone = int((po.status.cpu().numpy() != 6).sum())
+        entry["plain_launch"] = {"value": pdone / (a.elapsed_time(b) * 1e-3),
+                                 "unit": "zone-burns/s", "zones": Zp}
+    if sample_parity:
+        entry["sampled_parity"] = sampled_parity(name, net, z, s, out, sample_parity)
+    if cpu_zones:
+        base = cpu_baseline(name, cpu_zones)
+        base.pop("seconds", None)
+        entry["cpu_baseline"] = base
+    return entry
+
+
+def adjoint_bench(nb, torch, dev, flush, metrics, repeats=3) -> dict:
     """Adjoint gradients/s: the 48-species sensitivity workload, 6 cotangents
     per zone (energy + the 5 largest final abundances), forward with tape
-    plus reverse sweep."""
+    plus reverse sweep (which recomputes the checkpointed blocks), timed
+    `repeats` times, with the FP64 roofline of the reverse kernel."""
     name = "net48_adjoint"
     net, z, s = gen.problem(name)
     Z = z["T9"].shape[0]
@@ -413,24 +555,37 @@ def adjoint_bench(nb, torch, dev, flush, metrics) -> dict:
     gEd = torch.from_numpy(gE).to(dev)
     nb.adjoint(nc, tape, gYd, gEd)
     torch.cuda.synchronize()
-    flush.fill_(3.0)
-    a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-    a.record()
-    fw = nb.burn(nc, Y0, T9, rho, s["t_end"], s["rtol"], s["atol"], tape=tape)
-    b.record()
-    nb.adjoint(nc, tape, gYd, gEd)
-    c.record()
-    torch.cuda.synchronize()
-    fwd_ms, adj_ms = a.elapsed_time(b), b.elapsed_time(c)
+    fwd, rev = [], []
+    for k in range(repeats):
+        flush.fill_(3.0 + k)
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a.record()
+        fw = nb.burn(nc, Y0, T9, rho, s["t_end"], s["rtol"], s["atol"], tape=tape)
+        b.record()
+        nb.adjoint(nc, tape, gYd, gEd)
+        c.record()
+        torch.cuda.synchronize()
+        fwd.append(a.elapsed_time(b))
+        rev.append(b.elapsed_time(c))
+    fwd_ms, adj_ms = statistics.mean(fwd), statistics.mean(rev)
     st = fw.status.cpu().numpy()
-    steps = int(fw.counters.cpu().numpy()[:, 0].sum())
+    cnt = fw.counters.cpu().numpy()
+    steps = int(cnt[:, 0].sum())
     flops = metrics.adjoint_ops(info, steps, K, net.self_heating)
+    achieved = flops / (adj_ms * 1e-3) / 1e12
     return {"workload": "48 species / 180 rates, 16384 zones, T9 log-U[0.3,6], "
                         "rho log-U[1e4,1e9], t_end 1e-2, 6 cotangents per zone",
             "value": Z * K / ((fwd_ms + adj_ms) * 1e-3), "unit": "gradients/s",
             "gradient_length": net.R, "forward_ms": fwd_ms, "reverse_ms": adj_ms,
-            "zones_ok": int((st == 0).sum()),
-            "reverse_tflops": flops / (adj_ms * 1e-3) / 1e12}
+            "repeats": repeats, "forward_ms_each": fwd, "reverse_ms_each": rev,
+            "tape_checkpoint_stride": 16, "zones_ok": int((st == 0).sum()),
+            "roofline": {"bound": "alu", "kernel": "k_adjoint", "achieved": achieved,
+                         "peak": metrics.FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / metrics.FP64_PEAK_TFLOPS,
+                         "traffic": profiled_traffic("k_adjoint", Z, None, workload=name),
+                         "flops_per_launch": flops,
+                         "timed": "CUDA events around nb_burn_adjoint: the claim-order sort "
+                                  "and k_adjoint, which recomputes every checkpointed block"}}
 
 
 def multi_bench(nb, torch, dev, flush) -> dict:
@@ -479,8 +634,10 @@ def main():
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--sample-parity", type=int, default=0,
+    p.add_argument("--sample-parity", type=int, default=256,
                    help="check N seeded zones of the timed launch against the oracle")
+    p.add_argument("--configs", default="cfg0,cfg2,cfg4",
+                   help="comma-separated entries of the configuration table to add")
     p.add_argument("--t-end", type=float, default=None,
                    help="override t_end (profiling of a shorter burn only)")
     p.add_argument("--blocks-per-sm", type=int, default=0)

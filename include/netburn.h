@@ -66,6 +66,10 @@ extern "C" {
 #define NB_Z_NONFINITE 5     /* non-finite input, rate or first derivative */
 #define NB_Z_TIMEOUT 6       /* the call's time budget ran out before the zone
                                 finished (outputs: the state reached) */
+#define NB_Z_SINGULAR 7      /* 10 consecutive failed attempts, the last of them
+                                because the LU of alpha0 I - h J broke down: a
+                                zero or non-finite pivot, or a static pivot
+                                that lost more than 40 bits to cancellation */
 
 /* per-zone counters, counters[z * NB_NCOUNT + c] */
 #define NB_NCOUNT 8
@@ -200,12 +204,22 @@ typedef struct {
 
 #define NB_KERNEL_PERSISTENT 0  /* lane-per-zone, device work queue */
 #define NB_KERNEL_PLAIN 1       /* one thread per zone, no queue */
+#define NB_KERNEL_COOP 2        /* warp-per-zone, device work queue: the
+                                   zone's Newton-loop arrays in shared memory
+                                   and its vector, Jacobian and LU work spread
+                                   over the warp's lanes (large networks).
+                                   threads_per_block: warps per block x 32
+                                   (default: as many as fit, at most 4);
+                                   ws_in_shared 0: arrays in global memory */
 
 /* Compile a network: validate the topology, build the Jacobian sparsity
  * pattern, choose a minimum-degree elimination order, compute the LU fill
  * and the gather programs, and upload them to the current device.
  * coeffs: [R, 7] host array of (a0..a6).  *out receives a handle to free
- * with nb_net_free.  Synchronous. */
+ * with nb_net_free.  NB_E_TOO_LARGE when the state exceeds 4096 entries,
+ * the reactions 32767, or the pre-ordered LU fills the pattern of
+ * alpha0 I - h J to more than 4 times its nonzeros (nb_net_info reports
+ * both counts).  Synchronous. */
 int nb_net_load(const nb_topology* topo, const double* coeffs, nb_net* out);
 int nb_net_free(nb_net net);
 int nb_net_get_info(nb_net net, nb_net_info* out);

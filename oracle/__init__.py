@@ -30,7 +30,7 @@ N_COUNTERS = 8
 COUNTER_NAMES = ("accepted", "rejected_error", "rejected_newton", "newton_iters",
                  "jacobians", "rhs_evals", "rate_evals", "edot_evals")
 STATUS = {0: "OK", 1: "MAX_STEPS", 2: "DT_UNDERFLOW", 3: "NEWTON_FAIL",
-          5: "NONFINITE"}
+          5: "NONFINITE", 7: "SINGULAR"}
 
 
 def build(force: bool = False) -> str:

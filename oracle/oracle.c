@@ -103,7 +103,7 @@
 #define KMAX 5      /* highest BDF order */
 
 enum { ST_OK = 0, ST_MAX_STEPS = 1, ST_DT_UNDERFLOW = 2, ST_NEWTON_FAIL = 3,
-       ST_NONFINITE = 5 };
+       ST_NONFINITE = 5, ST_SINGULAR = 7 };
 
 /* per-zone event counters */
 enum { C_ACC = 0, C_REJ_ERR, C_REJ_NEWTON, C_NEWTON_IT, C_JAC, C_RHS, C_TEVAL,
@@ -808,7 +808,8 @@ static int burn_zone(const ora_network* net, const ora_options* opt,
         for (int i = 0; i < n; ++i)
             for (int j = 0; j < n; ++j)
                 W->M[i * n + j] = (i == j ? alpha[0] : 0.0) - h * W->J[i * n + j];
-        int ok = lu_factor(W->M, W->piv, n) == 0;
+        const int lu_ok = lu_factor(W->M, W->piv, n) == 0;
+        int ok = lu_ok;
         double nrm_prev = 0.0;
         int converged = 0;
         for (int m = 0; ok && m < opt->newton_maxit; ++m) {
@@ -833,7 +834,8 @@ static int burn_zone(const ora_network* net, const ora_options* opt,
         }
         if (!converged) {
             cnt[C_REJ_NEWTON]++;
-            if (++newton_fails >= 10) { status = ST_NEWTON_FAIL; break; }
+            /* ten in a row: SINGULAR when the last one's LU broke down */
+            if (++newton_fails >= 10) { status = lu_ok ? ST_NEWTON_FAIL : ST_SINGULAR; break; }
             h *= 0.25;
             continue;
         }

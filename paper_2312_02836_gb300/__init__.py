@@ -17,7 +17,7 @@ from typing import NamedTuple, Optional
 import numpy as np
 
 from . import _abi
-from ._abi import (COUNTER_NAMES, KERNEL_PERSISTENT, KERNEL_PLAIN, NCOUNT,
+from ._abi import (COUNTER_NAMES, KERNEL_COOP, KERNEL_PERSISTENT, KERNEL_PLAIN, NCOUNT,
                    ZONE_STATUS, NetburnError)
 
 __all__ = ["Network", "specialized_source", "specialize_compile", "burn", "burn_multi", "burn_host", "BurnGraph", "Tape", "adjoint", "Burn",
@@ -159,7 +159,8 @@ def _options(kernel, threads_per_block, blocks_per_sm, blob_in_shared,
     o = _abi.Options()
     _abi.load().nb_default_options(C.byref(o))
     if isinstance(kernel, str):
-        kernel = {"persistent": KERNEL_PERSISTENT, "plain": KERNEL_PLAIN}[kernel]
+        kernel = {"persistent": KERNEL_PERSISTENT, "plain": KERNEL_PLAIN,
+                  "coop": KERNEL_COOP}[kernel]
     o.kernel = int(kernel)
     o.threads_per_block = int(threads_per_block)
     o.blocks_per_sm = int(blocks_per_sm)

@@ -1,7 +1,8 @@
-"""Launch-shape autotuner for the persistent burn kernel.
+"""Launch-shape autotuner for the persistent burn kernels.
 
-The kernel maps one zone to one lane, so the tunables are which kernel runs,
-how many zones are in flight per SM and where their work arrays live:
+The tunables are which kernel runs (one zone per lane, generic or generated
+for the network, or one zone per warp), how many zones are in flight per SM
+and where their work arrays live:
 
 * ``specialize``: -1 the generic kernel, which walks the compiled network
   from memory; 1..3 the kernel generated for this network, with its work
@@ -15,7 +16,10 @@ how many zones are in flight per SM and where their work arrays live:
   only while few lanes are in flight;
 * ``threads_per_block`` and ``blocks_per_sm``: zones in flight.  Fewer lanes
   than zones let the device queue refill lanes whose zone finished; more
-  lanes hide more latency but grow the workspace beyond L2.
+  lanes hide more latency but grow the workspace beyond L2;
+* ``kernel="coop"`` (networks of 24 or more state entries): one warp per
+  zone with its Newton-loop arrays in shared memory; threads_per_block sets
+  the warps per block, hence the zones per SM that share its memory.
 
 Each candidate burns the caller's zones once and is timed with CUDA events
 on the current stream; the fastest wins.  Results are cached per network,
@@ -39,7 +43,14 @@ SPECIALIZED_CANDIDATES = tuple(
     dict(specialize=v, threads_per_block=tpb, blocks_per_sm=bps)
     for v in (1, 2, 3) for tpb, bps in ((64, 1), (128, 1), (128, 2), (256, 1)))
 
-DEFAULT_CANDIDATES = GENERIC_CANDIDATES + SPECIALIZED_CANDIDATES
+# one warp per zone, its Newton-loop arrays in shared memory (large networks)
+COOP_CANDIDATES = (
+    dict(kernel="coop", threads_per_block=0, blocks_per_sm=0),
+    dict(kernel="coop", threads_per_block=64, blocks_per_sm=0),
+    dict(kernel="coop", threads_per_block=32, blocks_per_sm=0),
+)
+
+DEFAULT_CANDIDATES = GENERIC_CANDIDATES + SPECIALIZED_CANDIDATES + COOP_CANDIDATES
 
 
 def autotune(net, Y0, T9, rho, t_end, rtol, atol, ln_mult=None, *,
@@ -59,8 +70,12 @@ def autotune(net, Y0, T9, rho, t_end, rtol, atol, ln_mult=None, *,
     stream = torch.cuda.current_stream(dev)
     best, best_ms, timings = None, float("inf"), []
     out = None
-    if not net.info()["specialize_auto"]:
+    info = net.info()
+    if not info["specialize_auto"]:
         candidates = [c for c in candidates if c.get("specialize", 0) < 0]
+    if info["n_state"] < 24:
+        # a warp per zone leaves most lanes idle on a small network
+        candidates = [c for c in candidates if c.get("kernel") != "coop"]
     for cand in candidates:
         try:
             out = burn(net, Y0, T9, rho, t_end, rtol, atol, ln_mult, out=out, **cand, **extra)

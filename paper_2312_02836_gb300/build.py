@@ -11,8 +11,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libnetburn.so")
 SOURCES = ["burn.cu", "adjoint.cu", "noalloc.cu", "multi.cu", "expcheck.cu", "netload.cpp",
            "codegen.cpp"]
-HEADERS = ["blob.h", "device.cuh", "integrator.cuh", "adjoint.cuh", "host.h", "expf64.cuh",
-           "codegen.h"]
+HEADERS = ["blob.h", "device.cuh", "integrator.cuh", "adjoint.cuh", "coop.cuh", "host.h",
+           "expf64.cuh", "codegen.h"]
 # headers the run-time compiler needs, embedded as text into the library
 # (name as written in the #include directive, path)
 EMBED = [("expf64.cuh", "csrc/expf64.cuh"), ("integrator.cuh", "csrc/integrator.cuh"),

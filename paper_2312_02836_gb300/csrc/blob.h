@@ -94,7 +94,13 @@ struct BlobHeader {
   int32_t o_tab_t9;     // double [tab_nt] T9 nodes
   int32_t o_tab_lnl;    // double [n_tab * tab_nd * tab_nt] ln lambda at the nodes
   int32_t o_charge;     // double [N] species charges
-  int32_t pad2_;
+  // column-oriented triangular solves (one zone spread over a warp)
+  int32_t o_perm;       // int16 [n] original index of position k
+  int32_t o_ltgt;       // int16 [nL] original row index of each L entry (lslot order)
+  int32_t o_ucol_ptr;   // int32 [n+1] entries of U column k (rows above k)
+  int32_t o_ucol_s;     // int16 [...] their slots
+  int32_t o_ucol_t;     // int16 [...] their original row indices
+  int32_t n_ucol;
 };
 
 }  // namespace nb

@@ -1,10 +1,12 @@
 // burn.cu -- kernels and C ABI of the batched reaction-network burn.
 //
-// Two launch shapes run the same per-zone integrator (device.cuh):
+// Three launch shapes run the same per-zone integrator (integrator.cuh):
 //  * persistent: a grid sized to the GPU (blocks_per_sm x SMs); every lane
 //    claims zones from a device work queue and claims the next one as soon as
 //    its zone finishes, so zones needing 10 or 10^4 steps share warps without
 //    idling the FP64 pipe;
+//  * cooperative: persistent too, but one warp per zone (coop.cuh), its
+//    Newton-loop arrays in shared memory: for large networks;
 //  * plain: one thread per zone, one launch over all zones (the comparison
 //    launch).
 #include <cuda_runtime.h>
@@ -20,6 +22,7 @@
 
 #include "blob.h"
 #include "codegen.h"
+#include "coop.cuh"
 #include "device.cuh"
 #include "../../include/netburn.h"
 
@@ -65,6 +68,36 @@ __global__ void __launch_bounds__(256, 1) k_burn_persistent(BurnParams P) {
                        (long long)(wib - P.smem_warps) * t.lane_doubles * WS_LANES + lane);
   }
   burn_claim_loop(t, w, P);
+}
+
+// One warp per zone.  With P.smem_warps > 0 every warp keeps the Newton-loop
+// part of its arrays in shared memory after the (optional) blob copy and
+// only the history in the global workspace; otherwise everything is in the
+// global workspace, lane_doubles per warp.
+__global__ void __launch_bounds__(256, 1) k_burn_coop(BurnParams P) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const unsigned char* blob = P.blob;
+  if (P.blob_in_smem) {
+    const int4* src = reinterpret_cast<const int4*>(P.blob);
+    int4* dst = reinterpret_cast<int4*>(sm);
+    for (int i = threadIdx.x; i < P.blob_bytes / 16; i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+    blob = sm;
+  }
+  const WNet t = make_wnet(blob, threadIdx.x & 31);
+  const int wib = threadIdx.x >> 5;
+  const long long warp = (long long)blockIdx.x * (blockDim.x >> 5) + wib;
+  double *hot, *cold;
+  if (P.smem_warps > 0) {
+    hot = reinterpret_cast<double*>(sm + (P.blob_in_smem ? P.blob_bytes : 0)) +
+          (size_t)wib * t.g.hot_doubles;
+    cold = P.ws + warp * (long long)(t.g.lane_doubles - t.g.hot_doubles);
+  } else {
+    hot = P.ws + warp * (long long)t.g.lane_doubles;
+    cold = hot + t.g.hot_doubles;
+  }
+  CWS w = make_cws(t.g, hot, cold);
+  coop_claim_loop(t, w, P);
 }
 
 // Scheduling pre-pass: each zone's starting step h0 (the integrator's own
@@ -338,6 +371,60 @@ static int schedule_longest_first(nb_net net, BurnParams& P, long long lanes,
   return NB_OK;
 }
 
+// The cooperative launch: one warp per zone.  threads_per_block (default:
+// the warps whose Newton-loop arrays fit in shared memory, at most 4 of
+// them) and blocks_per_sm set the zones in flight; ws_in_shared 0 keeps all
+// arrays in global memory, otherwise (default) in shared memory when they
+// fit; blob_in_shared as for the persistent kernel.
+static int launch_coop(nb_net net, BurnParams& P, const nb_options& o, cudaStream_t st) {
+  const size_t blob_b = (size_t)net->h.bytes;
+  const size_t hot_warp = (size_t)net->h.hot_doubles * sizeof(double);
+  const size_t warp_doubles = (size_t)net->h.lane_doubles;
+  const bool hot_smem = o.ws_in_shared != 0 && hot_warp <= net->smem_optin;
+  int in_smem = o.blob_in_shared;
+  if (in_smem < 0)
+    in_smem = blob_b <= 96 * 1024 && blob_b + (hot_smem ? hot_warp : 0) <= net->smem_optin;
+  const size_t fixed = in_smem ? blob_b : 0;
+  int wpb;
+  if (o.threads_per_block > 0) {
+    if (o.threads_per_block % 32 != 0 || o.threads_per_block > 256) return NB_E_ARG;
+    wpb = o.threads_per_block / 32;
+  } else {
+    wpb = 4;
+    if (hot_smem)
+      while (wpb > 1 && fixed + (size_t)wpb * hot_warp > net->smem_optin) --wpb;
+  }
+  const size_t dyn = fixed + (hot_smem ? (size_t)wpb * hot_warp : 0);
+  if (dyn > net->smem_optin) return NB_E_TOO_LARGE;
+  CK(cudaFuncSetAttribute(k_burn_coop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+  int occ = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_burn_coop, wpb * 32, dyn));
+  if (occ < 1) return NB_E_TOO_LARGE;
+  const int bps = std::max(1, std::min(o.blocks_per_sm > 0 ? o.blocks_per_sm : occ, occ));
+  long long blocks = (long long)bps * net->sm_count;
+  const long long needed = (P.Z + wpb - 1) / wpb;
+  if (blocks > needed) blocks = needed;
+  const size_t per_warp = (hot_smem ? warp_doubles - net->h.hot_doubles : warp_doubles) * 8;
+  size_t need = std::max<size_t>((size_t)blocks * wpb * per_warp, 256);
+  const size_t lane_bytes = warp_doubles * sizeof(double);
+  if (o.schedule == 1) need = std::max(need, (size_t)128 * lane_bytes);  // pre-pass lanes
+  int rc = nb::ensure((void**)&net->ws, &net->ws_bytes, need);
+  if (rc) return rc;
+  P.ws = net->ws;
+  P.queue = net->queue;
+  P.blob_in_smem = in_smem;
+  P.smem_warps = hot_smem ? wpb : 0;
+  P.order = nullptr;
+  if (o.schedule == 1 && P.Z > 1) {
+    rc = schedule_longest_first(net, P, 128, st);
+    if (rc) return rc;
+  }
+  CK(cudaMemsetAsync(net->queue, 0, sizeof(unsigned long long), st));
+  k_burn_coop<<<(unsigned)blocks, wpb * 32, dyn, st>>>(P);
+  CK(cudaGetLastError());
+  return NB_OK;
+}
+
 // Launch one burn (device pointers).  Caller holds net->mu.
 static int launch_burn(nb_net net, BurnParams& P, const nb_options& o,
                        cudaStream_t st) {
@@ -352,6 +439,7 @@ static int launch_burn(nb_net net, BurnParams& P, const nb_options& o,
   const size_t lane_bytes = (size_t)net->h.lane_doubles * sizeof(double);
   P.blob = net->d_blob;
   P.blob_bytes = net->h.bytes;
+  if (o.kernel == NB_KERNEL_COOP) return launch_coop(net, P, o, st);
   if (o.kernel == NB_KERNEL_PLAIN) {
     const long long blocks = (P.Z + tpb - 1) / tpb;
     const size_t need = (size_t)blocks * tpb * lane_bytes;

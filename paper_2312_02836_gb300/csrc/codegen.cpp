@@ -346,10 +346,12 @@ std::string specialized_source(const std::vector<uint8_t>& blob, int variant) {
 
   // ---- LU
   o("NB_HD __forceinline__ bool factor_M(const GNet&, GWS& w) {\n  bool ok = true;\n");
+  // the diagonal of M before elimination, for the pivot guard
+  for (int k = 0; k < n; ++k) o("  const double a%d = w.lu[%d];\n", k, piv[k].dslot);
   for (int k = 0; k < n; ++k) {
     const Pivot& p = piv[k];
-    o("  {\n    const double pv = w.lu[%d];\n    ok = ok && finite_nonzero(pv);\n"
-      "    const double inv = 1.0 / pv;\n    w.lu[%d] = inv;\n", p.dslot, p.dslot);
+    o("  {\n    const double pv = w.lu[%d];\n    ok = ok && pivot_kept(pv, a%d);\n"
+      "    const double inv = 1.0 / pv;\n    w.lu[%d] = inv;\n", p.dslot, k, p.dslot);
     const int nu = p.uend - p.ubeg;
     int dpos = p.dbeg;
     for (int li = p.lbeg; li < p.lend; ++li) {

@@ -316,13 +316,16 @@ NB_HD inline void assemble_M(const Net& t, const WS& w, const LV& v,
   }
 }
 
-// static-pivot LU in place; the diagonal keeps 1/pivot.  false if singular.
+// static-pivot LU in place; the diagonal keeps 1/pivot.  false if a pivot is
+// zero, not finite or eaten by cancellation (pivot_kept; the diagonal of M
+// before elimination is kept in w.tmp, free during an attempt)
 NB_HD inline bool factor_M(const Net& t, const WS& w) {
+  for (int k = 0; k < t.n; ++k) w.tmp[k] = w.lu[t.piv[k].dslot];
   bool ok = true;
   for (int k = 0; k < t.n; ++k) {
     const Pivot p = t.piv[k];
     const double pv = w.lu[p.dslot];
-    ok = ok && finite_nonzero(pv);
+    ok = ok && pivot_kept(pv, w.tmp[k]);
     const double inv = 1.0 / pv;
     w.lu[p.dslot] = inv;
     const int nu = p.uend - p.ubeg;

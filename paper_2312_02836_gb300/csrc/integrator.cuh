@@ -21,11 +21,16 @@
 //   assemble_M(t, w, v, alpha0, h)    lu = alpha0 I - h J(v)
 //   factor_M(t, w)                    static-pivot LU of lu in place
 //   solve_M(t, w, v)                  v <- M^-1 v with the factored lu
-// Two network types exist: the generic one (device.cuh) walks a compiled
+// Three network types exist: the generic one (device.cuh) walks a compiled
 // network held in memory; the specialised one is generated per network as
 // straight-line code with every index a constant and compiled at run time.
-// Both perform the same floating-point operations in the same order, so they
-// give the same bits.
+// Both run one zone per lane and perform the same floating-point operations
+// in the same order, so they give the same bits.  The cooperative one
+// (coop.cuh) runs one zone per warp: its vector loops are spread over the
+// 32 lanes (vbeg/vstep), its sums are warp reductions (vsum) and its phases
+// are separated by warp barriers (vsync); every lane holds the same copy of
+// the zone's scalars, so control flow stays uniform.  For the one-zone-per-
+// lane types these helpers reduce to the plain loops and do nothing.
 //
 // This header is also compiled by the run-time compiler, so it includes no
 // system header.
@@ -48,6 +53,41 @@
 #endif
 
 namespace nb {
+
+// Network types that spread one zone over the lanes of a warp specialise this
+template <class NT>
+struct is_coop {
+  static constexpr bool value = false;
+};
+
+// first index and stride of this thread's share of a vector loop
+template <class NT>
+NB_HD __forceinline__ constexpr int vbeg(const NT& t) {
+  if constexpr (is_coop<NT>::value) return t.lane; else return 0;
+}
+template <class NT>
+NB_HD __forceinline__ constexpr int vstep(const NT&) {
+  if constexpr (is_coop<NT>::value) return 32; else return 1;
+}
+// sum over the zone's threads of their partial sums (the same bits in all)
+template <class NT>
+NB_HD __forceinline__ double vsum(const NT& t, double x) {
+  if constexpr (is_coop<NT>::value) return t.sum(x); else return x;
+}
+template <class NT>
+NB_HD __forceinline__ bool vall(const NT& t, bool b) {
+  if constexpr (is_coop<NT>::value) return t.all(b); else return b;
+}
+// make the zone's vector writes visible to all its threads
+template <class NT>
+NB_HD __forceinline__ void vsync(const NT& t) {
+  if constexpr (is_coop<NT>::value) t.sync();
+}
+// the one thread that writes the zone's scalar outputs
+template <class NT>
+NB_HD __forceinline__ bool vlead(const NT& t) {
+  if constexpr (is_coop<NT>::value) return t.lane == 0; else return true;
+}
 
 // lane-strided view of one per-lane array
 struct LV {
@@ -140,6 +180,17 @@ NB_HD __forceinline__ bool finite_nonzero(double v) {
 }
 NB_HD __forceinline__ bool finite_bits(double v) {
   return (dbits(v) & 0x7fffffffffffffffLL) < 0x7ff0000000000000LL;
+}
+
+// Pivot guard of the static-pivot LU: pivot u_kk, finite and nonzero, has
+// not lost more than 40 bits to cancellation against the diagonal a_kk of M
+// before elimination (|u_kk| >= 2^-40 |a_kk|, on the exponents).  A static
+// pivot order cannot swap rows, so a pivot eaten by cancellation rejects the
+// attempt; the step then shrinks, and M = alpha0 I - h J tends to alpha0 I,
+// whose static pivots are safe.
+NB_HD __forceinline__ bool pivot_kept(double u, double a) {
+  const long long eu = (dbits(u) >> 52) & 0x7ff, ea = (dbits(a) >> 52) & 0x7ff;
+  return finite_nonzero(u) && eu + 40 >= ea;
 }
 
 // ---------------------------------------------------------------- model
@@ -326,6 +377,13 @@ NB_HD __forceinline__ double rate_near(double kref, double de) {
 // c_v = 1.5 sum_i Y_i + 1e-3 T9^3 (two interleaved partial sums)
 template <class NT, class V>
 NB_HD __forceinline__ double heat_capacity(const NT& t, const V& v) {
+  if constexpr (is_coop<NT>::value) {
+    double sy = 0.0;
+    for (int i = vbeg(t); i < t.N; i += vstep(t)) sy += v[i];
+    sy = vsum(t, sy);
+    const double T9 = v[t.N];
+    return 1.5 * sy + 1e-3 * T9 * T9 * T9;
+  }
   double s0 = 0.0, s1 = 0.0;
   int i = 0;
   NB_UNROLL
@@ -360,6 +418,14 @@ NB_HD __forceinline__ TRow t_row(double ed, double cv, double T9) {
 // compare squares, which spares a square root per norm)
 template <class NT, class WT, class V>
 NB_HD __forceinline__ double wnorm2(const NT& t, const WT& w, const V& v) {
+  if constexpr (is_coop<NT>::value) {
+    double sq = 0.0;
+    for (int i = vbeg(t); i < t.n; i += vstep(t)) {
+      const double q = v[i] * w.iw[i];
+      sq = fma(q, q, sq);
+    }
+    return vsum(t, sq) * t.inv_n;
+  }
   double s0 = 0.0, s1 = 0.0;
   int i = 0;
   NB_UNROLL
@@ -398,7 +464,7 @@ NB_HD __forceinline__ void hist_combine(const NT& t, const WT& w, int cnt, const
   NB_UNROLL
   for (int i = 0; i < NT::n; ++i) out[i] = acc[i];
 #else
-  for (int i = 0; i < t.n; ++i) {
+  for (int i = vbeg(t); i < t.n; i += vstep(t)) {
     double acc = 0.0;
     for (int j = 0; j < cnt; ++j) acc = fma(c[j], w.xh[base[j] + i], acc);
     out[i] = acc;
@@ -464,11 +530,11 @@ NB_HD __forceinline__ double order_estimate(const NT& t, const Zone& s, WT& w, i
   const int b0 = hslot(s, 0) * t.n;
   double acc = 0.0;
   NB_UNROLL
-  for (int i = 0; i < t.n; ++i) {
+  for (int i = vbeg(t); i < t.n; i += vstep(t)) {
     const double v = c * (w.xh[b0 + i] - w.tmp[i]) * w.iw[i];
     acc = fma(v, v, acc);
   }
-  return acc * t.inv_n;   // E_q^2
+  return vsum(t, acc) * t.inv_n;   // E_q^2
 }
 
 // Record an accepted point (time, step, order; state and energy when the
@@ -479,19 +545,22 @@ NB_HD __forceinline__ bool tape_record(const NT& t, const BurnParams& P, const Z
   if (!P.use_tape) return true;
   int32_t* cnt = P.tape.steps + s.z;
   const int idx = *cnt;
+  vsync(t);   // every thread has read the count before it moves on
   if (idx >= P.tape.cap) return false;
   const unsigned long long r = (unsigned long long)s.z * P.tape.cap + idx;
-  P.tape.sched[2 * r] = s.t;
-  P.tape.sched[2 * r + 1] = h;
-  P.tape.ord[r] = (int8_t)ord;
   const int slot = tape_state_slot(idx, P.tape.stride);
   if (slot >= 0) {
     double* rec = P.tape.states + ((unsigned long long)s.z * P.tape.scap + slot) * (t.n + 1);
     NB_UNROLL
-    for (int i = 0; i < t.n; ++i) rec[i] = x[i];
-    rec[t.n] = s.E;
+    for (int i = vbeg(t); i < t.n; i += vstep(t)) rec[i] = x[i];
+    if (vlead(t)) rec[t.n] = s.E;
   }
-  *cnt = idx + 1;
+  if (vlead(t)) {
+    P.tape.sched[2 * r] = s.t;
+    P.tape.sched[2 * r + 1] = h;
+    P.tape.ord[r] = (int8_t)ord;
+    *cnt = idx + 1;
+  }
   return true;
 }
 
@@ -541,12 +610,13 @@ NB_HD __forceinline__ bool zone_init(const NT& t, Zone& s, WT& w, const BurnPara
   bool fin = finite_bits(s.T9f) && s.T9f > 0.0 && finite_bits(s.rho) &&
              finite_bits(s.tend) && s.tend >= 0.0 && finite_bits(zeta) && zeta >= 0.0;
   NB_UNROLL
-  for (int i = 0; i < N; ++i) {
+  for (int i = vbeg(t); i < N; i += vstep(t)) {
     const double y = P.Y0[(unsigned long long)z * N + i];
     x0[i] = y;
     fin = fin && finite_bits(y);
   }
-  if (t.sh) x0[N] = s.T9f;
+  if (t.sh && vlead(t)) x0[N] = s.T9f;
+  vsync(t);
   tab_zone(t, s, x0);
   w.th[0] = 0.0;
   w.eh[0] = 0.0;
@@ -563,26 +633,30 @@ NB_HD __forceinline__ bool zone_init(const NT& t, Zone& s, WT& w, const BurnPara
   eval_f(t, w, x0, w.f0);
   s.c_rhs++;
   NB_UNROLL
-  for (int r = 0; r < t.R; ++r) fin = fin && finite_bits(w.k[r]);
+  for (int r = vbeg(t); r < t.R; r += vstep(t)) fin = fin && finite_bits(w.k[r]);
   NB_UNROLL
-  for (int i = 0; i < n; ++i) fin = fin && finite_bits(w.f0[i]);
+  for (int i = vbeg(t); i < n; i += vstep(t)) fin = fin && finite_bits(w.f0[i]);
+  fin = vall(t, fin);
   if (!fin) { s.status = NB_Z_NONFINITE; return true; }
   if (!(s.tend > 0.0)) return true;
   // starting step: Hairer-Norsett-Wanner I, Sec. II.4, p = 1
   double s0 = 0.0, s1 = 0.0;
   NB_UNROLL
-  for (int i = 0; i < n; ++i) {
+  for (int i = vbeg(t); i < n; i += vstep(t)) {
     const double iw = 1.0 / (P.atol + P.rtol * fabs(x0[i]));
     w.iw[i] = iw;
     const double a = x0[i] * iw, b = w.f0[i] * iw;
     s0 = fma(a, a, s0);
     s1 = fma(b, b, s1);
   }
+  s0 = vsum(t, s0);
+  s1 = vsum(t, s1);
   const double d0 = sqrt(s0 / n), d1 = sqrt(s1 / n);
   double hp = (d0 < 1e-5 || d1 < 1e-5) ? 1e-6 : 0.01 * d0 / d1;
   if (hp > s.tend) hp = s.tend;
   NB_UNROLL
-  for (int i = 0; i < n; ++i) w.x[i] = fma(hp, w.f0[i], x0[i]);
+  for (int i = vbeg(t); i < n; i += vstep(t)) w.x[i] = fma(hp, w.f0[i], x0[i]);
+  vsync(t);
   if (t.sh) {
     const double T9 = w.x[N];
     eval_rates(t, s, w, t_powers(T9, false, s.scr), T9, false);
@@ -594,10 +668,11 @@ NB_HD __forceinline__ bool zone_init(const NT& t, Zone& s, WT& w, const BurnPara
   double s2 = 0.0;
   const double ihp = 1.0 / hp;
   NB_UNROLL
-  for (int i = 0; i < n; ++i) {
+  for (int i = vbeg(t); i < n; i += vstep(t)) {
     const double q = (w.f[i] - w.f0[i]) * ihp * w.iw[i];
     s2 = fma(q, q, s2);
   }
+  s2 = vsum(t, s2);
   const double d2 = sqrt(s2 / n);
   const double dm = fmax(d1, d2);
   const double h1 = dm <= 1e-15 ? fmax(1e-6, hp * 1e-3) : sqrt(0.01 / dm);
@@ -621,8 +696,9 @@ NB_HD __forceinline__ bool zone_init(const NT& t, Zone& s, WT& w, const BurnPara
 template <class NT, class WT>
 NB_HD __forceinline__ bool attempt_solve(const NT& t, Zone& s, WT& w, double atol, double rtol,
                                          double h, double t_new, int kk, double* alpha,
-                                         TPow& pref, double& Tref) {
+                                         TPow& pref, double& Tref, bool& lu_ok) {
   const int n = t.n, N = t.N;
+  vsync(t);   // the history written by the last accepted step
   // alpha_j = h l_j'(t_new) over t_new, t_n, .., t_{n+1-kk}
   double tau[KMAX + 1];
   tau[0] = t_new;
@@ -637,7 +713,8 @@ NB_HD __forceinline__ bool attempt_solve(const NT& t, Zone& s, WT& w, double ato
     hist_combine(t, w, kk, alpha + 1, base, w.psi);
     const int b0 = hslot(s, 0) * n;
     NB_UNROLL
-    for (int i = 0; i < n; ++i) w.iw[i] = 1.0 / (atol + rtol * fabs(w.xh[b0 + i]));
+    for (int i = vbeg(t); i < n; i += vstep(t))
+      w.iw[i] = 1.0 / (atol + rtol * fabs(w.xh[b0 + i]));
   }
   // predictor
   if (s.nh >= kk + 1) extrapolate(t, s, w, 0, kk, t_new, w.xp);
@@ -645,10 +722,11 @@ NB_HD __forceinline__ bool attempt_solve(const NT& t, Zone& s, WT& w, double ato
   else {
     const int b0 = hslot(s, 0) * n;
     NB_UNROLL
-    for (int i = 0; i < n; ++i) w.xp[i] = fma(h, w.f0[i], w.xh[b0 + i]);
+    for (int i = vbeg(t); i < n; i += vstep(t)) w.xp[i] = fma(h, w.f0[i], w.xh[b0 + i]);
   }
   NB_UNROLL
-  for (int i = 0; i < n; ++i) w.x[i] = w.xp[i];
+  for (int i = vbeg(t); i < n; i += vstep(t)) w.x[i] = w.xp[i];
+  vsync(t);
   // Jacobian at the predictor, M, LU; with self-heating the predictor's
   // temperature is the attempt's reference for the rates
   Tref = 0.0;
@@ -663,6 +741,7 @@ NB_HD __forceinline__ bool attempt_solve(const NT& t, Zone& s, WT& w, double ato
   assemble_M(t, w, w.x, alpha[0], h);
   s.c_jac++;
   bool ok = factor_M(t, w);
+  lu_ok = ok;
   // modified Newton
   bool converged = false;
   double nrm_prev = 0.0;
@@ -674,11 +753,12 @@ NB_HD __forceinline__ bool attempt_solve(const NT& t, Zone& s, WT& w, double ato
     eval_f(t, w, w.x, w.f);
     s.c_rhs++;
     NB_UNROLL
-    for (int i = 0; i < n; ++i)
+    for (int i = vbeg(t); i < n; i += vstep(t))
       w.d[i] = -(fma(alpha[0], w.x[i], w.psi[i]) - h * w.f[i]);
     solve_M(t, w, w.d);
     NB_UNROLL
-    for (int i = 0; i < n; ++i) w.x[i] += w.d[i];
+    for (int i = vbeg(t); i < n; i += vstep(t)) w.x[i] += w.d[i];
+    vsync(t);
     s.c_newton++;
     const double nrm2 = wnorm2(t, w, w.d);
     if (!finite_bits(nrm2)) { ok = false; break; }
@@ -713,10 +793,12 @@ NB_HD __forceinline__ bool zone_attempt(const NT& t, Zone& s, WT& w, const BurnP
   double alpha[KMAX + 1];
   TPow pref;
   double Tref;
-  const bool converged = attempt_solve(t, s, w, P.atol, P.rtol, h, t_new, kk, alpha, pref, Tref);
+  bool lu_ok;
+  const bool converged =
+      attempt_solve(t, s, w, P.atol, P.rtol, h, t_new, kk, alpha, pref, Tref, lu_ok);
   if (!converged) {
     s.c_rej_newton++;
-    if (++s.nfail >= 10) { s.status = NB_Z_NEWTON_FAIL; return true; }
+    if (++s.nfail >= 10) { s.status = lu_ok ? NB_Z_NEWTON_FAIL : NB_Z_SINGULAR; return true; }
     s.h = h * 0.25;
     return false;
   }
@@ -727,11 +809,11 @@ NB_HD __forceinline__ bool zone_attempt(const NT& t, Zone& s, WT& w, const BurnP
   {
     double acc = 0.0;
     NB_UNROLL
-    for (int i = 0; i < n; ++i) {
+    for (int i = vbeg(t); i < n; i += vstep(t)) {
       const double v = c * (w.x[i] - w.xp[i]) * w.iw[i];
       acc = fma(v, v, acc);
     }
-    err2 = acc * t.inv_n;
+    err2 = vsum(t, acc) * t.inv_n;
   }
   if (!(err2 <= 1.0)) {
     s.c_rej_err++;
@@ -753,13 +835,17 @@ NB_HD __forceinline__ bool zone_attempt(const NT& t, Zone& s, WT& w, const BurnP
   }
   // push the new point into the history ring
   s.hh = s.hh == 0 ? HMAX - 1 : s.hh - 1;
+  vsync(t);   // every thread has read the ring's old scalars
   {
     const int b0 = s.hh * n;
     NB_UNROLL
-    for (int i = 0; i < n; ++i) w.xh[b0 + i] = w.x[i];
-    w.th[s.hh] = t_new;
-    w.eh[s.hh] = E_new;
+    for (int i = vbeg(t); i < n; i += vstep(t)) w.xh[b0 + i] = w.x[i];
+    if (vlead(t)) {
+      w.th[s.hh] = t_new;
+      w.eh[s.hh] = E_new;
+    }
   }
+  vsync(t);
   if (s.nh < HMAX) s.nh++;
   s.t = t_new;
   s.E = E_new;
@@ -805,13 +891,18 @@ NB_HD __forceinline__ bool replay_step(const NT& t, Zone& s, WT& w, double atol,
   double alpha[KMAX + 1];
   TPow pref;
   double Tref;
-  if (!attempt_solve(t, s, w, atol, rtol, h, t_new, kk, alpha, pref, Tref)) return false;
+  bool lu_ok;
+  if (!attempt_solve(t, s, w, atol, rtol, h, t_new, kk, alpha, pref, Tref, lu_ok)) return false;
   s.hh = s.hh == 0 ? HMAX - 1 : s.hh - 1;
+  vsync(t);
   const int b0 = s.hh * t.n;
   NB_UNROLL
-  for (int i = 0; i < t.n; ++i) w.xh[b0 + i] = w.x[i];
-  w.th[s.hh] = t_new;
-  w.eh[s.hh] = 0.0;
+  for (int i = vbeg(t); i < t.n; i += vstep(t)) w.xh[b0 + i] = w.x[i];
+  if (vlead(t)) {
+    w.th[s.hh] = t_new;
+    w.eh[s.hh] = 0.0;
+  }
+  vsync(t);
   if (s.nh < HMAX) s.nh++;
   s.t = t_new;
   return true;
@@ -832,8 +923,9 @@ NB_HD __forceinline__ unsigned long long gpu_ns() {
 template <class NT>
 NB_HD __forceinline__ void zone_timeout_unstarted(const NT& t, long long z,
                                                   const BurnParams& P) {
-  for (int i = 0; i < t.N; ++i)
+  for (int i = vbeg(t); i < t.N; i += vstep(t))
     P.Y[(unsigned long long)z * t.N + i] = P.Y0[(unsigned long long)z * t.N + i];
+  if (!vlead(t)) return;
   P.T9[z] = P.T9_0[z];
   if (P.E) P.E[z] = 0.0;
   P.status[z] = NB_Z_TIMEOUT;
@@ -848,8 +940,10 @@ NB_HD __forceinline__ void zone_finish(const NT& t, const Zone& s, const WT& w,
                                        const BurnParams& P) {
   const long long z = s.z;
   const int b0 = hslot(s, 0) * t.n;
+  vsync(t);
   NB_UNROLL
-  for (int i = 0; i < t.N; ++i) P.Y[(unsigned long long)z * t.N + i] = w.xh[b0 + i];
+  for (int i = vbeg(t); i < t.N; i += vstep(t)) P.Y[(unsigned long long)z * t.N + i] = w.xh[b0 + i];
+  if (!vlead(t)) return;
   P.T9[z] = t.sh ? w.xh[b0 + t.N] : s.T9f;
   if (P.E) P.E[z] = w.eh[s.hh];
   P.status[z] = s.status;

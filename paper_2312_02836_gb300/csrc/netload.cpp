@@ -173,7 +173,8 @@ int build_blob(const nb_topology* T, const double* coeffs,
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j)
       if (F[i][j]) slot[i][j] = nnz++;
-  if (nnz > 32767) return NB_E_TOO_LARGE;
+  // the pre-ordered LU may fill M's pattern to at most 4 times its nonzeros
+  if (nnz > 32767 || nnz > 4 * nnz_jac) return NB_E_TOO_LARGE;
 
   // Jacobian gather per slot; sources: dterm d (index d) or R_r g_r (nd + r)
   std::vector<int32_t> js_ptr(nnz + 1, 0);
@@ -263,6 +264,18 @@ int build_blob(const nb_topology* T, const double* coeffs,
   tri(false, true, true, &tbw, &tbw_s, &tbw_c);   // L^T u = v
   std::vector<int32_t> diag_orig(n);
   for (int i = 0; i < n; ++i) diag_orig[i] = slot[pos[i]][pos[i]];
+  // column-oriented solves: rows of the L entries, and U by columns
+  std::vector<int16_t> perm16(n), ltgt, ucol_s, ucol_t;
+  std::vector<int32_t> ucol_ptr(n + 1, 0);
+  for (int k = 0; k < n; ++k) perm16[k] = (int16_t)perm[k];
+  for (int k = 0; k < n; ++k)
+    for (int i = k + 1; i < n; ++i)
+      if (F[i][k]) ltgt.push_back((int16_t)perm[i]);
+  for (int k = 0; k < n; ++k) {
+    for (int i = 0; i < k; ++i)
+      if (F[i][k]) { ucol_s.push_back((int16_t)slot[i][k]); ucol_t.push_back((int16_t)perm[i]); }
+    ucol_ptr[k + 1] = (int32_t)ucol_s.size();
+  }
 
   // adjoint: species entries of each rate, d f_i / d p_r = c_ir R_r
   std::vector<int32_t> rg_ptr(R + 1, 0);
@@ -383,6 +396,12 @@ int build_blob(const nb_topology* T, const double* coeffs,
   h.o_rg_ptr = B.add(rg_ptr);
   h.o_rg_i = B.add(rg_i);
   h.o_rg_c = B.add(rg_c);
+  h.o_perm = B.add(perm16);
+  h.o_ltgt = B.add(ltgt);
+  h.o_ucol_ptr = B.add(ucol_ptr);
+  h.o_ucol_s = B.add(ucol_s);
+  h.o_ucol_t = B.add(ucol_t);
+  h.n_ucol = (int32_t)ucol_s.size();
   h.nL = (int32_t)lslot.size(); h.nU = (int32_t)uslot.size(); h.nD = (int32_t)dslot.size();
   h.n_rhs = (int32_t)rhs_r.size(); h.n_js = (int32_t)js_src.size();
   h.n_fw = (int32_t)fw_s.size(); h.n_bw = (int32_t)bw_s.size();

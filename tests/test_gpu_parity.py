@@ -62,10 +62,11 @@ CASES = [("chain13", 4096), ("chain13_literal", 1024), ("chain13_heat", 2048),
 
 # "persistent": the default persistent launch (the network-specialised kernel
 # where the network qualifies); "generic": the persistent launch forced onto
-# the generic kernel; "plain": one thread per zone
+# the generic kernel; "plain": one thread per zone; "coop": one warp per zone
 KERNELS = {"persistent": dict(kernel="persistent"),
            "generic": dict(kernel="persistent", specialize="generic"),
-           "plain": dict(kernel="plain")}
+           "plain": dict(kernel="plain"),
+           "coop": dict(kernel="coop")}
 
 
 @pytest.mark.parametrize("kernel", list(KERNELS))
@@ -168,6 +169,15 @@ def test_deterministic_and_order_independent():
     for k in a:
         for other in (d, e, f, g):
             assert np.array_equal(a[k], other[k])
+    # the warp-per-zone kernel: deterministic, independent of the claim order
+    # and of where its arrays live (its solves and sums round differently from
+    # the lane kernels', so it is compared with the oracle elsewhere)
+    c1 = gpu_run(nb, torch, net_c, z, s, kernel="coop")
+    c2 = gpu_run(nb, torch, net_c, zp, s, kernel="coop", threads_per_block=64)
+    c3 = gpu_run(nb, torch, net_c, z, s, kernel="coop", ws_in_shared=0, blob_in_shared=0)
+    for k in a:
+        assert np.array_equal(c1[k][perm], c2[k])
+        assert np.array_equal(c1[k], c3[k])
 
 
 def test_rate_multipliers_shared_and_per_zone():
