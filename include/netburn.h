@@ -242,6 +242,17 @@ int nb_burn_batch(nb_net net, int64_t Z, const double* Y0, const double* T9_0,
                   double* T9, double* E, int32_t* counters, int32_t* status,
                   const nb_options* opt, void* tape, void* stream);
 
+/* Predicted cost of burning each zone, for splitting zones across GPUs
+ * with balanced work (the paper's zones sit on a hydro grid, where burn
+ * cost follows the local temperature and density, so equal zone counts
+ * need not be equal work).  cost [Z] device output: (1 + ln(t_end/h0))^2,
+ * h0 the starting step of the integrator's own start-up (0 for a zone that
+ * finishes in start-up).  Arguments as for nb_burn_batch; from opt:
+ * t_end_zone and zeta_zone.  Asynchronous on stream. */
+int nb_zone_costs(nb_net net, int64_t Z, const double* Y0, const double* T9_0,
+                  const double* rho, double t_end, double rtol, double atol,
+                  const nb_options* opt, double* cost, void* stream);
+
 /* Same burn from HOST arrays (pageable or pinned): copies the inputs to
  * library-owned device buffers, burns, copies the outputs back and waits
  * for the stream.  Synchronous.  E, counters may be NULL. */

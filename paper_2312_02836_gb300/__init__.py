@@ -20,7 +20,7 @@ from . import _abi
 from ._abi import (COUNTER_NAMES, KERNEL_COOP, KERNEL_PERSISTENT, KERNEL_PLAIN, NCOUNT,
                    ZONE_STATUS, NetburnError)
 
-__all__ = ["Network", "specialized_source", "specialize_compile", "burn", "burn_multi", "burn_host", "BurnGraph", "Tape", "adjoint", "Burn",
+__all__ = ["Network", "specialized_source", "specialize_compile", "burn", "burn_multi", "burn_host", "BurnGraph", "Tape", "adjoint", "Burn", "zone_costs",
            "BurnResult", "NetburnError", "COUNTER_NAMES", "ZONE_STATUS",
            "KERNEL_PERSISTENT", "KERNEL_PLAIN", "library_path"]
 
@@ -242,6 +242,31 @@ def burn(net: Network, Y0, T9, rho, t_end: float, rtol: float, atol: float,
     if tape is not None:
         tape._recorded(Z, ln_mult, float(t_end), float(rtol), float(atol))
     return out
+
+
+def zone_costs(net: Network, Y0, T9, rho, t_end, rtol, atol, *, zeta=None, stream=None):
+    """Predicted cost of burning each zone (``nb_zone_costs``), a CUDA
+    float64 tensor [Z]: the weights ``parallel.shard`` balances."""
+    torch = _torch()
+    Z = int(Y0.shape[0])
+    _dev(Y0, torch, "Y0", (Z, net.N))
+    _dev(T9, torch, "T9", (Z,))
+    _dev(rho, torch, "rho", (Z,))
+    cost = torch.empty(Z, dtype=torch.float64, device=Y0.device)
+    o = _options("persistent", 0, 0, -1, 500000)
+    if isinstance(t_end, torch.Tensor):
+        _dev(t_end, torch, "t_end", (Z,))
+        o.t_end_zone = t_end.data_ptr()
+        t_end = 0.0
+    if zeta is not None:
+        _dev(zeta, torch, "zeta", (Z,))
+        o.zeta_zone = zeta.data_ptr()
+    st = stream if stream is not None else torch.cuda.current_stream(Y0.device)
+    _abi.check(_abi.load().nb_zone_costs(net.handle, Z, Y0.data_ptr(), T9.data_ptr(),
+                                         rho.data_ptr(), float(t_end), float(rtol), float(atol),
+                                         C.byref(o), cost.data_ptr(), C.c_void_p(st.cuda_stream)),
+               "nb_zone_costs")
+    return cost
 
 
 def burn_multi(sets, t_end: float, rtol: float, atol: float, *, threads_per_block=0,

@@ -28,7 +28,7 @@ EXPORTS = ("nb_net_load", "nb_net_free", "nb_net_get_info", "nb_default_options"
            "nb_tape_steps", "nb_tape_read", "nb_burn_adjoint", "nb_burn_batch_noalloc",
            "nb_burn_multi", "nb_net_specialize", "nb_specialize_source",
            "nb_specialize_compile",
-           "nb_exp_eval", "nb_strerror")
+           "nb_exp_eval", "nb_zone_costs", "nb_strerror")
 
 
 class Topology(C.Structure):
@@ -112,6 +112,8 @@ def load(build_if_needed: bool = True):
         lib.nb_specialize_compile.argtypes = [P, P, I32, P, I64]
         lib.nb_specialize_compile.restype = C.c_int
         lib.nb_exp_eval.argtypes = [P, P, P, I64, P]
+        lib.nb_zone_costs.argtypes = [P, I64, P, P, P, D, D, D, P, P, P]
+        lib.nb_zone_costs.restype = C.c_int
         lib.nb_exp_eval.restype = C.c_int
         lib.nb_strerror.argtypes = [C.c_int]
         lib.nb_strerror.restype = C.c_char_p
