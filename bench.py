@@ -568,6 +568,17 @@ def adjoint_bench(nb, torch, dev, flush, metrics, repeats=3) -> dict:
         fwd.append(a.elapsed_time(b))
         rev.append(b.elapsed_time(c))
     fwd_ms, adj_ms = statistics.mean(fwd), statistics.mean(rev)
+    # the same with every state on the tape (stride 1): no recomputation
+    full = nb.Tape(nc, Z, 4000, 1)
+    nb.burn(nc, Y0, T9, rho, s["t_end"], s["rtol"], s["atol"], tape=full)
+    flush.fill_(9.0)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    nb.adjoint(nc, full, gYd, gEd)
+    b.record()
+    torch.cuda.synchronize()
+    full_ms = a.elapsed_time(b)
+    del full
     st = fw.status.cpu().numpy()
     cnt = fw.counters.cpu().numpy()
     steps = int(cnt[:, 0].sum())
@@ -579,10 +590,14 @@ def adjoint_bench(nb, torch, dev, flush, metrics, repeats=3) -> dict:
             "gradient_length": net.R, "forward_ms": fwd_ms, "reverse_ms": adj_ms,
             "repeats": repeats, "forward_ms_each": fwd, "reverse_ms_each": rev,
             "tape_checkpoint_stride": 16, "zones_ok": int((st == 0).sum()),
-            "roofline": {"bound": "alu", "kernel": "k_adjoint", "achieved": achieved,
+            "reverse_ms_full_tape": full_ms,
+            "adjoint_kernel": "k_adjoint_coop" if net.N >= 24 else "k_adjoint",
+            "roofline": {"bound": "alu", "kernel": "k_adjoint_coop" if net.N >= 24 else "k_adjoint",
+                         "achieved": achieved,
                          "peak": metrics.FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / metrics.FP64_PEAK_TFLOPS,
-                         "traffic": profiled_traffic("k_adjoint", Z, None, workload=name),
+                         "traffic": profiled_traffic("k_adjoint_coop" if net.N >= 24 else "k_adjoint",
+                                                     Z, None, workload=name),
                          "flops_per_launch": flops,
                          "timed": "CUDA events around nb_burn_adjoint: the claim-order sort "
                                   "and k_adjoint, which recomputes every checkpointed block"}}

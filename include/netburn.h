@@ -307,6 +307,19 @@ int nb_tape_read(void* tape, int64_t z, int32_t cap, double* t, double* h,
 int nb_burn_adjoint(nb_net net, void* tape, int32_t K, const double* gY,
                     const double* gE, const double* gT9, double* d_ln_mult,
                     double* dY0, double* dT0, void* stream);
+/* nb_burn_adjoint with launch options (opt NULL: as nb_burn_adjoint, which
+ * runs one warp per zone for networks of 24 or more state entries and one
+ * lane per zone below).  From opt: kernel (NB_KERNEL_PERSISTENT one lane per
+ * zone, NB_KERNEL_COOP one warp per zone), threads_per_block (lane kernel at
+ * most 128; warp kernel: warps per block x 32, at most 256, default as many
+ * as fit in shared memory up to 4), blocks_per_sm, ws_in_shared (0: the
+ * warp kernel keeps its arrays in global memory) and blob_in_shared (0: the
+ * warp kernel reads the network from global memory).  Every kernel and
+ * launch shape gives the same gradients up to the rounding of the
+ * transposed solves and sums. */
+int nb_burn_adjoint_ex(nb_net net, void* tape, int32_t K, const double* gY,
+                       const double* gE, const double* gT9, double* d_ln_mult,
+                       double* dY0, double* dT0, const nb_options* opt, void* stream);
 
 /* Burn without any device allocation.  The paper has no counterpart: this is
  * for callers that may not allocate device memory while they run the burn

@@ -446,9 +446,12 @@ class Tape:
 
 
 def adjoint(net: Network, tape: Tape, gY, gE=None, gT9=None, *, stream=None,
-            want_initial=True):
+            want_initial=True, kernel="auto", threads_per_block=0, blocks_per_sm=0,
+            ws_in_shared=-1, blob_in_shared=-1):
     """Discrete adjoint of the burn recorded on ``tape``.  gY [K,Z,N], gE and
-    gT9 [K,Z] (or None).  Returns (d_ln_mult [K,Z,R], dY0 [K,Z,N], dT0 [K,Z])."""
+    gT9 [K,Z] (or None).  kernel: "auto" (one warp per zone for networks of
+    24 or more state entries), "persistent" (one lane per zone) or "coop".
+    Returns (d_ln_mult [K,Z,R], dY0 [K,Z,N], dT0 [K,Z])."""
     torch = _torch()
     if tape.recorded is None:
         raise NetburnError("tape holds no burn")
@@ -469,10 +472,15 @@ def adjoint(net: Network, tape: Tape, gY, gE=None, gT9=None, *, stream=None,
     dT0 = torch.empty((K, Z), dtype=torch.float64, device=dev) if want_initial else None
     st = stream if stream is not None else torch.cuda.current_stream(dev)
     ptr = lambda t: None if t is None else t.data_ptr()
-    rc = _abi.load().nb_burn_adjoint(net.handle, tape.handle, K, ptr(gY), ptr(gE),
-                                     ptr(gT9), ptr(dl), ptr(dY0), ptr(dT0),
-                                     C.c_void_p(st.cuda_stream))
-    _abi.check(rc, "nb_burn_adjoint")
+    o = None
+    if kernel != "auto":
+        o = _options(kernel, threads_per_block, blocks_per_sm, blob_in_shared, 500000,
+                     ws_in_shared)
+    rc = _abi.load().nb_burn_adjoint_ex(net.handle, tape.handle, K, ptr(gY), ptr(gE),
+                                        ptr(gT9), ptr(dl), ptr(dY0), ptr(dT0),
+                                        None if o is None else C.byref(o),
+                                        C.c_void_p(st.cuda_stream))
+    _abi.check(rc, "nb_burn_adjoint_ex")
     return dl, dY0, dT0
 
 

@@ -25,7 +25,7 @@ KERNEL_COOP = 2
 # every symbol declared in include/netburn.h
 EXPORTS = ("nb_net_load", "nb_net_free", "nb_net_get_info", "nb_default_options",
            "nb_burn_batch", "nb_burn_batch_host", "nb_tape_alloc", "nb_tape_free",
-           "nb_tape_steps", "nb_tape_read", "nb_burn_adjoint", "nb_burn_batch_noalloc",
+           "nb_tape_steps", "nb_tape_read", "nb_burn_adjoint", "nb_burn_adjoint_ex", "nb_burn_batch_noalloc",
            "nb_burn_multi", "nb_net_specialize", "nb_specialize_source",
            "nb_specialize_compile",
            "nb_exp_eval", "nb_zone_costs", "nb_strerror")
@@ -100,6 +100,8 @@ def load(build_if_needed: bool = True):
         lib.nb_tape_free.argtypes = [P]
         lib.nb_tape_steps.argtypes = [P, P]
         lib.nb_burn_adjoint.argtypes = [P, P, I32, P, P, P, P, P, P, P]
+        lib.nb_burn_adjoint_ex.argtypes = [P, P, I32, P, P, P, P, P, P, P, P]
+        lib.nb_burn_adjoint_ex.restype = C.c_int
         lib.nb_burn_batch_noalloc.argtypes = [P, I64, P, P, P, D, D, D, P, I32, P,
                                               P, P, P, P, P, P]
         lib.nb_burn_batch_noalloc.restype = C.c_int

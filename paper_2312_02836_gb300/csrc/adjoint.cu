@@ -18,7 +18,9 @@
 // in blocks of the tape's stride, last block first, recomputes each block's
 // states forward from its checkpointed history window with the forward's
 // own step computation (attempt_solve, so the same bits), then reverses it.
-// One lane per zone, K cotangent sets share each LU factorisation.
+// One lane per zone (k_adjoint), or one warp per zone for large networks
+// (k_adjoint_coop: the same per-zone code with the network spread over the
+// warp, coop.cuh); K cotangent sets share each LU factorisation.
 #include <cuda_runtime.h>
 #include <cub/device/device_radix_sort.cuh>
 
@@ -27,6 +29,7 @@
 
 #include "blob.h"
 #include "adjoint.cuh"
+#include "coop.cuh"
 #include "device.cuh"
 #include "host.h"
 #include "../../include/netburn.h"
@@ -96,6 +99,57 @@ __global__ void __launch_bounds__(128) k_adjoint(AdjParams A) {
   }
 }
 
+// One warp per zone.  With A.blob_in_smem > 1 the warp's Newton-loop arrays
+// and its adjoint arrays sit in shared memory after the (optional) blob
+// copy: [forward hot | adjoint] per warp, adj_doubles of adjoint arrays.
+struct CoopAdj {
+  int smem;           // arrays in shared memory
+  int adj_doubles;    // adjoint arrays per zone
+};
+
+__global__ void __launch_bounds__(256, 1) k_adjoint_coop(AdjParams A, CoopAdj C) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const unsigned char* blob = A.blob;
+  if (A.blob_in_smem) {
+    const int4* src = reinterpret_cast<const int4*>(A.blob);
+    int4* dst = reinterpret_cast<int4*>(sm);
+    for (int i = threadIdx.x; i < A.blob_bytes / 16; i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+    blob = sm;
+  }
+  const WNet t = make_wnet(blob, threadIdx.x & 31);
+  const int wib = threadIdx.x >> 5;
+  const long long warp = (long long)blockIdx.x * (blockDim.x >> 5) + wib;
+  const long long fwd = t.g.lane_doubles;
+  CWS w;
+  AWST<CV> a;
+  if (C.smem) {
+    double* hot = reinterpret_cast<double*>(sm + (A.blob_in_smem ? A.blob_bytes : 0)) +
+                  (size_t)wib * (t.g.hot_doubles + C.adj_doubles);
+    w = make_cws(t.g, hot, A.ws + warp * (fwd - t.g.hot_doubles));
+    a = make_aws_at<CV>(A, hot + t.g.hot_doubles - fwd, 1);
+  } else {
+    double* base = A.ws + warp * A.lane_doubles;
+    w = make_cws(t.g, base, base + t.g.hot_doubles);
+    a = make_aws_at<CV>(A, base, 1);
+  }
+  for (;;) {
+    unsigned long long c = 0;
+    if (t.lane == 0) c = atomicAdd(A.queue, 1ull);
+    c = __shfl_sync(kFullMask, c, 0);
+    if (c >= (unsigned long long)A.Z) break;
+    AdjZone Zs;
+    Zs.z = A.order ? (long long)A.order[c] : (long long)c;
+    Zs.rs = 1;
+    Zs.re = 0;
+    Zs.lo = 1;
+    bool done = adj_init(t, Zs, w, a, A);
+    while (!done) done = Zs.rs <= Zs.re ? adj_replay(t, Zs, w, a, A) : adj_step(t, Zs, w, a, A);
+    adj_finish(t, Zs, a, A);
+    __syncwarp();
+  }
+}
+
 __global__ void k_zone_index(int32_t* idx, long long Z) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < Z) idx[i] = (int32_t)i;
@@ -106,6 +160,13 @@ __global__ void k_zone_index(int32_t* idx, long long Z) {
 extern "C" int nb_burn_adjoint(nb_net net, void* tape, int32_t K, const double* gY,
                                const double* gE, const double* gT9, double* d_ln_mult,
                                double* dY0, double* dT0, void* stream) {
+  return nb_burn_adjoint_ex(net, tape, K, gY, gE, gT9, d_ln_mult, dY0, dT0, nullptr, stream);
+}
+
+extern "C" int nb_burn_adjoint_ex(nb_net net, void* tape, int32_t K, const double* gY,
+                                  const double* gE, const double* gT9, double* d_ln_mult,
+                                  double* dY0, double* dT0, const nb_options* opt,
+                                  void* stream) {
   if (!net || !tape || K < 1 || K > 64 || !gY || !d_ln_mult) return NB_E_ARG;
   nb_tape_s* tp = (nb_tape_s*)tape;
   if (tp->magic != 0x7a9e5eedu || tp->net != net || !tp->recorded) return NB_E_TAPE;
@@ -135,24 +196,71 @@ extern "C" int nb_burn_adjoint(nb_net net, void* tape, int32_t K, const double* 
   A.o_de = (int)off; off += n;
   A.o_seg = (int)off; off += (long long)tp->dev.stride * n;
   A.lane_doubles = off;
-  // one zone per lane; smaller blocks when there are few zones per SM
-  const long long per_sm = (Z + net->sm_count - 1) / net->sm_count;
-  const int tpb = per_sm >= 128 ? 128 : (int)std::max(32LL, per_sm / 32 * 32);
+  nb_options o;
+  nb_default_options(&o);
+  if (opt) o = *opt;
+  // the kernel: as asked, else one warp per zone from 24 state entries on
+  int kernel = opt ? o.kernel : (n >= 24 ? NB_KERNEL_COOP : NB_KERNEL_PERSISTENT);
+  if (kernel != NB_KERNEL_COOP && kernel != NB_KERNEL_PERSISTENT) return NB_E_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   std::lock_guard<std::mutex> lk(net->mu);
-  const size_t smem = (size_t)h.bytes;
-  const int in_smem = smem <= 96 * 1024 ? 1 : 0;
-  const size_t dyn = in_smem ? smem : 0;
-  if (dyn > 48 * 1024)
-    CK(cudaFuncSetAttribute(k_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
-  int occ = 0;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_adjoint, tpb, dyn));
-  long long blocks = (long long)std::max(1, std::min(occ, 2)) * net->sm_count;
-  const long long needed = (Z + tpb - 1) / tpb;
-  if (blocks > needed) blocks = needed;
-  const size_t need = (size_t)blocks * tpb * A.lane_doubles * sizeof(double);
-  int rc = nb::ensure((void**)&net->ws_adj, &net->ws_adj_bytes, need);
-  if (rc) return rc;
+  const size_t blob_b = (size_t)h.bytes;
+  int tpb, in_smem;
+  size_t dyn;
+  long long blocks;
+  CoopAdj C{0, (int)(A.lane_doubles - h.lane_doubles)};
+  size_t per_unit;   // global workspace per lane (lane kernel) or warp (coop)
+  if (kernel == NB_KERNEL_COOP) {
+    // per warp in shared memory: the forward hot arrays and the adjoint's
+    const size_t warp_b = ((size_t)h.hot_doubles + C.adj_doubles) * sizeof(double);
+    int wpb = o.threads_per_block > 0 ? o.threads_per_block / 32 : 0;
+    if (o.threads_per_block % 32 != 0 || wpb > 8) return NB_E_ARG;
+    in_smem = 0;
+    C.smem = o.ws_in_shared != 0 && warp_b <= net->smem_optin;
+    if (wpb == 0) {
+      wpb = 4;
+      if (C.smem) while (wpb > 1 && (size_t)wpb * warp_b > net->smem_optin) --wpb;
+    }
+    if (o.blob_in_shared != 0 && blob_b <= 96 * 1024 &&
+        blob_b + (C.smem ? wpb * warp_b : 0) <= net->smem_optin)
+      in_smem = 1;
+    dyn = (in_smem ? blob_b : 0) + (C.smem ? wpb * warp_b : 0);
+    if (dyn > net->smem_optin) return NB_E_TOO_LARGE;
+    tpb = wpb * 32;
+    CK(cudaFuncSetAttribute(k_adjoint_coop, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)dyn));
+    int occ = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_adjoint_coop, tpb, dyn));
+    if (occ < 1) return NB_E_TOO_LARGE;
+    const int bps = std::max(1, std::min(o.blocks_per_sm > 0 ? o.blocks_per_sm : occ, occ));
+    blocks = (long long)bps * net->sm_count;
+    const long long needed = (Z + wpb - 1) / wpb;
+    if (blocks > needed) blocks = needed;
+    per_unit = (C.smem ? (size_t)(h.lane_doubles - h.hot_doubles) : (size_t)A.lane_doubles) * 8;
+    const size_t need = (size_t)blocks * wpb * per_unit;
+    int rc = nb::ensure((void**)&net->ws_adj, &net->ws_adj_bytes, std::max<size_t>(need, 256));
+    if (rc) return rc;
+  } else {
+    // one zone per lane; smaller blocks when there are few zones per SM
+    const long long per_sm = (Z + net->sm_count - 1) / net->sm_count;
+    tpb = o.threads_per_block > 0 ? o.threads_per_block
+                                  : (per_sm >= 128 ? 128 : (int)std::max(32LL, per_sm / 32 * 32));
+    if (tpb % 32 != 0 || tpb > 128) return NB_E_ARG;
+    in_smem = blob_b <= 96 * 1024 ? 1 : 0;
+    dyn = in_smem ? blob_b : 0;
+    if (dyn > 48 * 1024)
+      CK(cudaFuncSetAttribute(k_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    int occ = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_adjoint, tpb, dyn));
+    blocks = (long long)std::max(1, std::min(o.blocks_per_sm > 0 ? o.blocks_per_sm : 2, occ)) *
+             net->sm_count;
+    const long long needed = (Z + tpb - 1) / tpb;
+    if (blocks > needed) blocks = needed;
+    per_unit = (size_t)A.lane_doubles * sizeof(double);
+    int rc = nb::ensure((void**)&net->ws_adj, &net->ws_adj_bytes, (size_t)blocks * tpb * per_unit);
+    if (rc) return rc;
+  }
+  int rc = NB_OK;
   A.ws = net->ws_adj;
   A.queue = net->queue + 1;   // a second counter in the same allocation
   A.blob_in_smem = in_smem;
@@ -179,7 +287,10 @@ extern "C" int nb_burn_adjoint(nb_net net, void* tape, int32_t K, const double* 
     A.order = i_out;
   }
   CK(cudaMemsetAsync(A.queue, 0, sizeof(unsigned long long), st));
-  k_adjoint<<<(unsigned)blocks, tpb, dyn, st>>>(A);
+  if (kernel == NB_KERNEL_COOP)
+    k_adjoint_coop<<<(unsigned)blocks, tpb, dyn, st>>>(A, C);
+  else
+    k_adjoint<<<(unsigned)blocks, tpb, dyn, st>>>(A);
   CK(cudaGetLastError());
   return NB_OK;
 }

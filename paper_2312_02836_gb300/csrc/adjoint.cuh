@@ -38,8 +38,8 @@ struct AdjParams {
 // Reverse-sweep state of one zone.  The steps are taken in blocks of the
 // tape's stride C, last block first: steps lo..re of the current block are
 // recomputed forward (rs is the next one) from the checkpointed history
-// window at record lo - 1, their states kept in the lane's segment buffer,
-// and then reversed from s down to lo.
+// window at record lo - 1, their states kept in the segment buffer, and
+// then reversed from s down to lo.
 struct AdjZone {
   long long z;
   int s;        // next step to reverse
@@ -55,43 +55,66 @@ NB_HD __forceinline__ const double* sched_ptr(const AdjParams& A, long long z, i
 }
 
 // state and energy of kept record q
-NB_HD __forceinline__ const double* state_ptr(const Net& t, const AdjParams& A,
-                                                   long long z, int q) {
-  return A.tape.states + ((size_t)z * A.tape.scap + tape_state_slot(q, A.tape.stride)) *
-                             (t.n + 1);
+NB_HD __forceinline__ const double* state_ptr(int n, const AdjParams& A, long long z, int q) {
+  return A.tape.states + ((size_t)z * A.tape.scap + tape_state_slot(q, A.tape.stride)) * (n + 1);
 }
 
-struct AWS {
-  LV lam, ee, gr, gt, mu, de, seg;
+// The adjoint's own arrays of one zone, views of type V (lane-strided for
+// one zone per lane, contiguous for one zone per warp)
+template <class V>
+struct AWST {
+  V lam, ee, gr, gt, mu, de, seg;
 };
+using AWS = AWST<LV>;
 
-NB_HD __forceinline__ AWS make_aws(const AdjParams& A, double* lane_base) {
-  AWS a;
-  a.lam.p = lane_base + (size_t)A.o_lam * WS_LANES;
-  a.ee.p = lane_base + (size_t)A.o_ee * WS_LANES;
-  a.gr.p = lane_base + (size_t)A.o_gr * WS_LANES;
-  a.gt.p = lane_base + (size_t)A.o_gt * WS_LANES;
-  a.mu.p = lane_base + (size_t)A.o_mu * WS_LANES;
-  a.de.p = lane_base + (size_t)A.o_de * WS_LANES;
-  a.seg.p = lane_base + (size_t)A.o_seg * WS_LANES;
+template <class V>
+NB_HD __forceinline__ AWST<V> make_aws_at(const AdjParams& A, double* base, int stride) {
+  AWST<V> a;
+  a.lam.p = base + (size_t)A.o_lam * stride;
+  a.ee.p = base + (size_t)A.o_ee * stride;
+  a.gr.p = base + (size_t)A.o_gr * stride;
+  a.gt.p = base + (size_t)A.o_gt * stride;
+  a.mu.p = base + (size_t)A.o_mu * stride;
+  a.de.p = base + (size_t)A.o_de * stride;
+  a.seg.p = base + (size_t)A.o_seg * stride;
   return a;
 }
+
+NB_HD __forceinline__ AWS make_aws(const AdjParams& A, double* lane_base) {
+  return make_aws_at<LV>(A, lane_base, WS_LANES);
+}
+
+// the compiled network of either network type
+NB_HD __forceinline__ const Net& net_of(const Net& t) { return t; }
+template <class NT>
+NB_HD __forceinline__ const Net& net_of(const NT& t) { return t.g; }
 
 // Set up the recomputation of the block holding step s_hi: load its history
 // window (records q0, q0-1, .. with q0 = the block's start) from the tape
 // into the forward history ring, as the forward burn held it before step
 // q0 + 1.
-NB_HD inline void seg_start(const Net& t, AdjZone& Zs, const WS& w, const AdjParams& A, int s_hi) {
+template <class NT, class WT>
+NB_HD inline void seg_start(const NT& t, AdjZone& Zs, WT& w, const AdjParams& A, int s_hi) {
   const int C = A.tape.stride;
   const int q0 = (s_hi - 1) / C * C;
+  if (C == 1) {   // every state is on the tape: nothing to recompute
+    Zs.lo = s_hi;
+    Zs.rs = s_hi + 1;
+    Zs.re = s_hi;
+    return;
+  }
   Zone& s = Zs.fz;
   const int nh = q0 + 1 < HMAX ? q0 + 1 : HMAX;
+  vsync(t);
   for (int i = 0; i < nh; ++i) {
-    const double* st = state_ptr(t, A, Zs.z, q0 - i);
-    for (int e = 0; e < t.n; ++e) w.xh[i * t.n + e] = st[e];
-    w.eh[i] = st[t.n];
-    w.th[i] = sched_ptr(A, Zs.z, q0 - i)[0];
+    const double* st = state_ptr(t.n, A, Zs.z, q0 - i);
+    for (int e = vbeg(t); e < t.n; e += vstep(t)) w.xh[i * t.n + e] = st[e];
+    if (vlead(t)) {
+      w.eh[i] = st[t.n];
+      w.th[i] = sched_ptr(A, Zs.z, q0 - i)[0];
+    }
   }
+  vsync(t);
   s.hh = 0;
   s.nh = nh;
   s.t = w.th[0];
@@ -107,26 +130,31 @@ NB_HD inline void seg_start(const Net& t, AdjZone& Zs, const WS& w, const AdjPar
 }
 
 // returns true when the zone needs no reverse steps
-NB_HD inline bool adj_init(const Net& t, AdjZone& Zs, const WS& w, const AWS& a,
-                         const AdjParams& A) {
+template <class NT, class WT, class AT>
+NB_HD inline bool adj_init(const NT& t, AdjZone& Zs, WT& w, const AT& a, const AdjParams& A) {
   const long long z = Zs.z;
   const int n = t.n, N = t.N, K = A.K;
   const int st = A.tape.zstat[z];
   const int S = A.tape.steps[z] - 1;
-  for (int e = 0; e < HMAX * K * n; ++e) a.lam[e] = 0.0;
-  for (int e = 0; e < HMAX * K; ++e) a.ee[e] = 0.0;
-  for (int e = 0; e < K * t.R; ++e) a.gr[e] = 0.0;
-  for (int q = 0; q < K; ++q) a.gt[q] = 0.0;
+  vsync(t);
+  for (int e = vbeg(t); e < HMAX * K * n; e += vstep(t)) a.lam[e] = 0.0;
+  for (int e = vbeg(t); e < HMAX * K; e += vstep(t)) a.ee[e] = 0.0;
+  for (int e = vbeg(t); e < K * t.R; e += vstep(t)) a.gr[e] = 0.0;
+  for (int q = vbeg(t); q < K; q += vstep(t)) a.gt[q] = 0.0;
   Zs.fail = false;
   Zs.s = (st == NB_Z_OK && S >= 0) ? S : -1;
+  vsync(t);
   if (Zs.s < 0) return true;
   const int sl = ring(S);
   for (int q = 0; q < K; ++q) {
     const size_t qz = (size_t)q * A.Z + z;
-    for (int i = 0; i < N; ++i) a.lam[(sl * K + q) * n + i] = A.gY[qz * N + i];
-    if (t.sh) a.lam[(sl * K + q) * n + N] = A.gT9 ? A.gT9[qz] : 0.0;
-    a.ee[sl * K + q] = A.gE ? A.gE[qz] : 0.0;
+    for (int i = vbeg(t); i < N; i += vstep(t)) a.lam[(sl * K + q) * n + i] = A.gY[qz * N + i];
+    if (vlead(t)) {
+      if (t.sh) a.lam[(sl * K + q) * n + N] = A.gT9 ? A.gT9[qz] : 0.0;
+      a.ee[sl * K + q] = A.gE ? A.gE[qz] : 0.0;
+    }
   }
+  vsync(t);
   Zone& s = Zs.fz;
   s.z = z;
   s.rho = A.tape.rho[z];
@@ -137,7 +165,7 @@ NB_HD inline bool adj_init(const Net& t, AdjZone& Zs, const WS& w, const AWS& a,
   s.k = 1;
   s.c_acc = s.c_rej_err = s.c_rej_newton = s.c_newton = 0;
   s.c_jac = s.c_rhs = s.c_teval = s.c_edot = 0;
-  tab_zone(t, s, state_ptr(t, A, z, 0));   // the recorded initial state
+  tab_zone(t, s, state_ptr(n, A, z, 0));   // the recorded initial state
   s.lnm = A.lnm ? (A.lnm_per_zone ? A.lnm + (size_t)z * t.R : A.lnm) : nullptr;
   // fixed temperature: the rates of the whole burn (with their T9 slopes)
   if (!t.sh) eval_rates(t, s, w, t_powers(s.T9f, true, s.scr), s.T9f, true);
@@ -147,8 +175,8 @@ NB_HD inline bool adj_init(const Net& t, AdjZone& Zs, const WS& w, const AWS& a,
 }
 
 // Recompute the next step of the current block; false when the zone is done.
-NB_HD inline bool adj_replay(const Net& t, AdjZone& Zs, const WS& w, const AWS& a,
-                           const AdjParams& A) {
+template <class NT, class WT, class AT>
+NB_HD inline bool adj_replay(const NT& t, AdjZone& Zs, WT& w, const AT& a, const AdjParams& A) {
   const int q = Zs.rs;
   const double* sc = sched_ptr(A, Zs.z, q);
   const int kk = A.tape.ord[(size_t)Zs.z * A.tape.cap + q];
@@ -158,14 +186,57 @@ NB_HD inline bool adj_replay(const Net& t, AdjZone& Zs, const WS& w, const AWS& 
   }
   const int b0 = Zs.fz.hh * t.n;
   const int o = (q - Zs.lo) * t.n;
-  for (int e = 0; e < t.n; ++e) a.seg[o + e] = w.xh[b0 + e];
+  for (int e = vbeg(t); e < t.n; e += vstep(t)) a.seg[o + e] = w.xh[b0 + e];
   Zs.rs = q + 1;
   return false;
 }
 
+// d edot / dx into a.de (needs w.dt at x): per species, its derivative terms
+// in increasing order (the order a scatter over the terms adds them in)
+template <class NT, class WT, class AT>
+NB_HD __forceinline__ void edot_gradient(const NT& t, const WT& w, const AT& a) {
+  const Net& g = net_of(t);
+  if constexpr (is_coop<NT>::value) {
+    for (int j = vbeg(t); j < t.N; j += vstep(t)) {
+      double acc = 0.0;
+      for (int e = t.dej_ptr[j]; e < t.dej_ptr[j + 1]; ++e) {
+        const int d = t.dej_d[e];
+        acc += g.Q[g.dt_r[d]] * w.dt[d];
+      }
+      a.de[j] = acc;
+    }
+    if (t.sh) {
+      double acc = 0.0;
+      for (int r = vbeg(t); r < t.R; r += vstep(t)) acc = fma(g.Q[r], w.dt[g.nd + r], acc);
+      acc = vsum(t, acc);
+      if (vlead(t)) a.de[t.N] = acc;
+    }
+  } else {
+    for (int i = 0; i < t.n; ++i) a.de[i] = 0.0;
+    for (int d = 0; d < g.nd; ++d) a.de[g.dt_j[d]] += g.Q[g.dt_r[d]] * w.dt[d];
+    if (t.sh) {
+      double acc = 0.0;
+      for (int r = 0; r < t.R; ++r) acc = fma(g.Q[r], w.dt[g.nd + r], acc);
+      a.de[t.N] = acc;
+    }
+  }
+  vsync(t);
+}
+
+// v <- M^-T v with the factored LU of either network type
+NB_HD __forceinline__ void solve_MT_of(const Net& t, const LV& lu, const LV& v) {
+  tri_solve(t.tfw, t.tfw_s, t.tfw_c, t.n, lu, v);
+  tri_solve(t.tbw, t.tbw_s, t.tbw_c, t.n, lu, v);
+}
+template <class NT, class LUV, class V>
+NB_HD __forceinline__ void solve_MT_of(const NT& t, const LUV& lu, const V& v) {
+  solve_MT(t, lu, v);
+}
+
 // reverse one step; returns true when the zone is done
-NB_HD inline bool adj_step(const Net& t, AdjZone& Zs, const WS& w, const AWS& a,
-                         const AdjParams& A) {
+template <class NT, class WT, class AT>
+NB_HD inline bool adj_step(const NT& t, AdjZone& Zs, WT& w, const AT& a, const AdjParams& A) {
+  const Net& g = net_of(t);
   const long long z = Zs.z;
   const int n = t.n, N = t.N, K = A.K, s = Zs.s;
   const double* ss = sched_ptr(A, z, s);
@@ -178,22 +249,21 @@ NB_HD inline bool adj_step(const Net& t, AdjZone& Zs, const WS& w, const AWS& a,
   double alpha[KMAX + 1];
   bdf_alpha(kk, tau, h, alpha);
   const int o = (s - Zs.lo) * n;
-  for (int i = 0; i < n; ++i) w.x[i] = a.seg[o + i];
+  vsync(t);
+  if (A.tape.stride == 1) {
+    const double* xs = state_ptr(n, A, z, s);
+    for (int i = vbeg(t); i < n; i += vstep(t)) w.x[i] = xs[i];
+  } else {
+    for (int i = vbeg(t); i < n; i += vstep(t)) w.x[i] = a.seg[o + i];
+  }
+  vsync(t);
   if (t.sh) eval_rates(t, Zs.fz, w, t_powers(w.x[N], true, Zs.fz.scr), w.x[N], true);
   eval_terms(t, w, w.x);
   assemble_M(t, w, w.x, alpha[0], h);
   factor_M(t, w);
   double icv = 0.0;
   if (t.sh) icv = 1.0 / heat_capacity(t, w.x);
-  if (t.hasE) {
-    for (int i = 0; i < n; ++i) a.de[i] = 0.0;
-    for (int d = 0; d < t.nd; ++d) a.de[t.dt_j[d]] += t.Q[t.dt_r[d]] * w.dt[d];
-    if (t.sh) {
-      double acc = 0.0;
-      for (int r = 0; r < t.R; ++r) acc = fma(t.Q[r], w.dt[t.nd + r], acc);
-      a.de[N] = acc;
-    }
-  }
+  if (t.hasE) edot_gradient(t, w, a);
   const double ia0 = 1.0 / alpha[0];
   const int sl = ring(s);
   int sj[KMAX + 1];
@@ -203,36 +273,39 @@ NB_HD inline bool adj_step(const Net& t, AdjZone& Zs, const WS& w, const AWS& a,
     const int lo = (sl * K + q) * n;
     const double es = a.ee[sl * K + q];
     const double ce = es * h * ia0;
-    for (int i = 0; i < n; ++i) {
+    for (int i = vbeg(t); i < n; i += vstep(t)) {
       double v = a.lam[lo + i];
       if (t.hasE) v = fma(ce, a.de[i], v);
       a.mu[i] = v;
       a.lam[lo + i] = 0.0;
     }
-    a.ee[sl * K + q] = 0.0;
-    tri_solve(t.tfw, t.tfw_s, t.tfw_c, n, w.lu, a.mu);
-    tri_solve(t.tbw, t.tbw_s, t.tbw_c, n, w.lu, a.mu);
+    vsync(t);
+    if (vlead(t)) a.ee[sl * K + q] = 0.0;
+    solve_MT_of(t, w.lu, a.mu);
+    vsync(t);
 #pragma unroll
     for (int j = 1; j <= KMAX; ++j) {
       if (j > kk) continue;
       const int lj = (sj[j] * K + q) * n;
       const double ma = -alpha[j];
-      for (int i = 0; i < n; ++i) a.lam[lj + i] = fma(ma, a.mu[i], a.lam[lj + i]);
-      if (t.hasE) a.ee[sj[j] * K + q] = fma(-es * ia0, alpha[j], a.ee[sj[j] * K + q]);
+      for (int i = vbeg(t); i < n; i += vstep(t)) a.lam[lj + i] = fma(ma, a.mu[i], a.lam[lj + i]);
+      if (t.hasE && vlead(t)) a.ee[sj[j] * K + q] = fma(-es * ia0, alpha[j], a.ee[sj[j] * K + q]);
     }
     const double muT = t.sh ? a.mu[N] * icv : 0.0;
     double gt = 0.0;
-    for (int r = 0; r < t.R; ++r) {
+    for (int r = vbeg(t); r < t.R; r += vstep(t)) {
       double acc = 0.0;
-      for (int e = t.rg_ptr[r]; e < t.rg_ptr[r + 1]; ++e)
-        acc = fma(t.rg_c[e], a.mu[t.rg_i[e]], acc);
-      const double Qr = t.Q[r];
+      for (int e = g.rg_ptr[r]; e < g.rg_ptr[r + 1]; ++e)
+        acc = fma(g.rg_c[e], a.mu[g.rg_i[e]], acc);
+      const double Qr = g.Q[r];
       acc = fma(muT, Qr, acc);
       const double v = w.rr[r] * fma(h, acc, ce * Qr);
       a.gr[q * t.R + r] += v;
       if (!t.sh) gt = fma(v, w.g[r], gt);
     }
-    a.gt[q] += gt;
+    gt = vsum(t, gt);
+    if (vlead(t)) a.gt[q] += gt;
+    vsync(t);
   }
   Zs.s = s - 1;
   if (Zs.s == 0) return true;
@@ -240,8 +313,8 @@ NB_HD inline bool adj_step(const Net& t, AdjZone& Zs, const WS& w, const AWS& a,
   return false;
 }
 
-NB_HD inline void adj_finish(const Net& t, const AdjZone& Zs, const AWS& a,
-                           const AdjParams& A) {
+template <class NT, class AT>
+NB_HD inline void adj_finish(const NT& t, const AdjZone& Zs, const AT& a, const AdjParams& A) {
   const long long z = Zs.z;
   const int n = t.n, N = t.N, K = A.K;
   const bool ok = Zs.s == 0 && !Zs.fail;
@@ -249,12 +322,14 @@ NB_HD inline void adj_finish(const Net& t, const AdjZone& Zs, const AWS& a,
   // not finish gets zero gradients
   const double bad = Zs.fail ? quiet_nan() : 0.0;
   const int s0 = ring(0);
+  vsync(t);
   for (int q = 0; q < K; ++q) {
     const size_t qz = (size_t)q * A.Z + z;
-    for (int r = 0; r < t.R; ++r) A.dl[qz * t.R + r] = ok ? a.gr[q * t.R + r] : bad;
+    for (int r = vbeg(t); r < t.R; r += vstep(t)) A.dl[qz * t.R + r] = ok ? a.gr[q * t.R + r] : bad;
     if (A.dY0)
-      for (int i = 0; i < N; ++i) A.dY0[qz * N + i] = ok ? a.lam[(s0 * K + q) * n + i] : bad;
-    if (A.dT0) A.dT0[qz] = ok ? (t.sh ? a.lam[(s0 * K + q) * n + N] : a.gt[q]) : bad;
+      for (int i = vbeg(t); i < N; i += vstep(t))
+        A.dY0[qz * N + i] = ok ? a.lam[(s0 * K + q) * n + i] : bad;
+    if (A.dT0 && vlead(t)) A.dT0[qz] = ok ? (t.sh ? a.lam[(s0 * K + q) * n + N] : a.gt[q]) : bad;
   }
 }
 

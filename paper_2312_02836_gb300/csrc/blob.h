@@ -101,6 +101,14 @@ struct BlobHeader {
   int32_t o_ucol_s;     // int16 [...] their slots
   int32_t o_ucol_t;     // int16 [...] their original row indices
   int32_t n_ucol;
+  // transposed solves of the adjoint, column by column
+  int32_t o_utgt;       // int16 [nU] original column index of each U entry (uslot order)
+  int32_t o_lrow_ptr;   // int32 [n+1] entries of L row k (columns left of k)
+  int32_t o_lrow_s;     // int16 [...] their slots
+  int32_t o_lrow_t;     // int16 [...] their original column indices
+  int32_t o_dej_ptr;    // int32 [n+1] derivative terms taken by species j
+  int32_t o_dej_d;      // int16 [nd] those terms, in increasing order
+  int32_t n_lrow, pad3_;
 };
 
 }  // namespace nb

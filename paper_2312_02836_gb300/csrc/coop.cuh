@@ -36,8 +36,8 @@ struct WNet {
   int n, N, R, sh, hasE;
   double inv_n;
   int lane;
-  const int16_t *perm, *ltgt, *ucol_s, *ucol_t;
-  const int32_t* ucol_ptr;
+  const int16_t *perm, *ltgt, *ucol_s, *ucol_t, *utgt, *lrow_s, *lrow_t, *dej_d;
+  const int32_t *ucol_ptr, *lrow_ptr, *dej_ptr;
   // sum over the warp, the same bits in every lane (an xor butterfly adds
   // the same two operands in both lanes of each pair)
   __device__ __forceinline__ double sum(double x) const {
@@ -66,6 +66,12 @@ __device__ __forceinline__ WNet make_wnet(const unsigned char* blob, int lane) {
   t.ucol_ptr = at<int32_t>(blob, h->o_ucol_ptr);
   t.ucol_s = at<int16_t>(blob, h->o_ucol_s);
   t.ucol_t = at<int16_t>(blob, h->o_ucol_t);
+  t.utgt = at<int16_t>(blob, h->o_utgt);
+  t.lrow_ptr = at<int32_t>(blob, h->o_lrow_ptr);
+  t.lrow_s = at<int16_t>(blob, h->o_lrow_s);
+  t.lrow_t = at<int16_t>(blob, h->o_lrow_t);
+  t.dej_ptr = at<int32_t>(blob, h->o_dej_ptr);
+  t.dej_d = at<int16_t>(blob, h->o_dej_d);
   return t;
 }
 
@@ -282,6 +288,34 @@ __device__ __forceinline__ void solve_M(const WNet& t, const CWS& w, const CV& v
     for (int e = t.ucol_ptr[k] + t.lane; e < t.ucol_ptr[k + 1]; e += 32) {
       const int r = t.ucol_t[e];
       v[r] = fma(-w.lu[t.ucol_s[e]], xk, v[r]);
+    }
+    __syncwarp();
+  }
+}
+
+// v <- M^-T v with the factored w.lu (the adjoint): U^T column by column
+// (pivot rows of U), then L^T column by column from the last (rows of L)
+template <class V>
+__device__ __forceinline__ void solve_MT(const WNet& t, const CV& lu, const V& v) {
+  __syncwarp();
+  const Net& g = t.g;
+  for (int k = 0; k < t.n; ++k) {
+    const Pivot p = g.piv[k];
+    const int pk = t.perm[k];
+    const double xk = v[pk] * lu[p.dslot];
+    __syncwarp();
+    if (t.lane == 0) v[pk] = xk;
+    for (int u = p.ubeg + t.lane; u < p.uend; u += 32) {
+      const int r = t.utgt[u];
+      v[r] = fma(-lu[g.uslot[u]], xk, v[r]);
+    }
+    __syncwarp();
+  }
+  for (int k = t.n - 1; k >= 0; --k) {
+    const double xk = v[t.perm[k]];
+    for (int e = t.lrow_ptr[k] + t.lane; e < t.lrow_ptr[k + 1]; e += 32) {
+      const int r = t.lrow_t[e];
+      v[r] = fma(-lu[t.lrow_s[e]], xk, v[r]);
     }
     __syncwarp();
   }

@@ -276,6 +276,17 @@ int build_blob(const nb_topology* T, const double* coeffs,
       if (F[i][k]) { ucol_s.push_back((int16_t)slot[i][k]); ucol_t.push_back((int16_t)perm[i]); }
     ucol_ptr[k + 1] = (int32_t)ucol_s.size();
   }
+  // transposed solves: the columns of the U entries (pivot rows), L by rows
+  std::vector<int16_t> utgt, lrow_s, lrow_t;
+  std::vector<int32_t> lrow_ptr(n + 1, 0);
+  for (int k = 0; k < n; ++k)
+    for (int j = k + 1; j < n; ++j)
+      if (F[k][j]) utgt.push_back((int16_t)perm[j]);
+  for (int k = 0; k < n; ++k) {
+    for (int i = 0; i < k; ++i)
+      if (F[k][i]) { lrow_s.push_back((int16_t)slot[k][i]); lrow_t.push_back((int16_t)perm[i]); }
+    lrow_ptr[k + 1] = (int32_t)lrow_s.size();
+  }
 
   // adjoint: species entries of each rate, d f_i / d p_r = c_ir R_r
   std::vector<int32_t> rg_ptr(R + 1, 0);
@@ -402,6 +413,23 @@ int build_blob(const nb_topology* T, const double* coeffs,
   h.o_ucol_s = B.add(ucol_s);
   h.o_ucol_t = B.add(ucol_t);
   h.n_ucol = (int32_t)ucol_s.size();
+  h.o_utgt = B.add(utgt);
+  h.o_lrow_ptr = B.add(lrow_ptr);
+  h.o_lrow_s = B.add(lrow_s);
+  h.o_lrow_t = B.add(lrow_t);
+  h.n_lrow = (int32_t)lrow_s.size();
+  {
+    // derivative terms by the species they are taken by (state index j < N)
+    std::vector<int32_t> dej_ptr(n + 1, 0);
+    std::vector<int16_t> dej_d;
+    for (int j = 0; j < n; ++j) {
+      for (int d = 0; d < nd; ++d)
+        if (dt_j[d] == j) dej_d.push_back((int16_t)d);
+      dej_ptr[j + 1] = (int32_t)dej_d.size();
+    }
+    h.o_dej_ptr = B.add(dej_ptr);
+    h.o_dej_d = B.add(dej_d);
+  }
   h.nL = (int32_t)lslot.size(); h.nU = (int32_t)uslot.size(); h.nD = (int32_t)dslot.size();
   h.n_rhs = (int32_t)rhs_r.size(); h.n_js = (int32_t)js_src.size();
   h.n_fw = (int32_t)fw_s.size(); h.n_bw = (int32_t)bw_s.size();

@@ -29,7 +29,7 @@ def nb_mod():
 
 
 def gpu_forward_adjoint(nb, torch, net, z, s, gY, gE, gT9, ln_mult=None, max_steps=6000,
-                        stride=1):
+                        stride=1, kernel="auto"):
     """Forward with a tape, then the adjoint; returns the adjoint outputs,
     the forward outputs and the tape."""
     dev = torch.device("cuda")
@@ -41,7 +41,7 @@ def gpu_forward_adjoint(nb, torch, net, z, s, gY, gE, gT9, ln_mult=None, max_ste
                  torch.from_numpy(z["rho"]).to(dev), s["t_end"], s["rtol"], s["atol"], lm,
                  tape=tape, zeta=torch.from_numpy(z["zeta"]).to(dev) if "zeta" in z else None)
     t = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).to(dev)
-    dl, dY0, dT0 = nb.adjoint(nc, tape, t(gY), t(gE), t(gT9))
+    dl, dY0, dT0 = nb.adjoint(nc, tape, t(gY), t(gE), t(gT9), kernel=kernel)
     torch.cuda.synchronize()
     out = dict(dl=dl.cpu().numpy(), dY0=dY0.cpu().numpy(), dT0=dT0.cpu().numpy(),
                counters=fw.counters.cpu().numpy(), Y=fw.Y.cpu().numpy(),
@@ -53,15 +53,20 @@ CASES = [("net48_adjoint", 16), ("chain13_heat", 48), ("chain13_heat_scr", 24),
          ("chain13_heat_ap", 24), ("chain13_heat_tab", 24)]
 
 
+# the adjoint kernels: one lane per zone, one warp per zone
+ADJ_KERNELS = ("persistent", "coop")
+
+
+@pytest.mark.parametrize("kernel", ADJ_KERNELS)
 @pytest.mark.parametrize("name,Z", CASES)
-def test_adjoint_matches_forward_sensitivity_on_gpu_trajectory(name, Z):
+def test_adjoint_matches_forward_sensitivity_on_gpu_trajectory(name, Z, kernel):
     nb, torch = nb_mod()
     net, z, s = gen.problem(name, Z)
     o = oracle.burn(net, z["Y"], z["T9"], z["rho"], s["t_end"], s["rtol"], s["atol"],
                     zeta=z.get("zeta"))
     gY, gE = cotangents(net, o["Y"], Z)
     gT9 = np.zeros((6, Z)) if net.self_heating else None
-    out, tape, nc = gpu_forward_adjoint(nb, torch, net, z, s, gY, gE, gT9)
+    out, tape, nc = gpu_forward_adjoint(nb, torch, net, z, s, gY, gE, gT9, kernel=kernel)
     assert (out["status"] == 0).all()
     sens = oracle_sensitivities(net, z, tape.read, range(Z))
     lit = tot = 0
@@ -69,12 +74,13 @@ def test_adjoint_matches_forward_sensitivity_on_gpu_trajectory(name, Z):
         a, b = check_zone(net, gY, gE, gT9, out, sens, i)
         lit += a
         tot += b
-    print(name, f"entries beyond 1e-10 relative (within the measured spread): {lit}/{tot}")
+    print(name, kernel, f"entries beyond 1e-10 relative (within the measured spread): {lit}/{tot}")
 
 
+@pytest.mark.parametrize("kernel", ADJ_KERNELS)
 @pytest.mark.parametrize("name,Z", [("chain13_heat", 64), ("net48_adjoint", 16),
                                     ("chain13_heat_tab", 32)])
-def test_checkpointed_tape_gives_the_full_tape_bits(name, Z):
+def test_checkpointed_tape_gives_the_full_tape_bits(name, Z, kernel):
     # the reverse sweep recomputes every block from its checkpoint with the
     # forward's own step computation: any stride gives the same bits
     nb, torch = nb_mod()
@@ -83,9 +89,10 @@ def test_checkpointed_tape_gives_the_full_tape_bits(name, Z):
     gY = rng.normal(size=(2, Z, net.N))
     gE = rng.normal(size=(2, Z)) if net.Q is not None else None
     gT9 = rng.normal(size=(2, Z)) if net.self_heating else None
-    ref, tp1, _ = gpu_forward_adjoint(nb, torch, net, z, s, gY, gE, gT9, stride=1)
+    ref, tp1, _ = gpu_forward_adjoint(nb, torch, net, z, s, gY, gE, gT9, stride=1, kernel=kernel)
     for stride in (3, 16, 0):
-        out, tp, _ = gpu_forward_adjoint(nb, torch, net, z, s, gY, gE, gT9, stride=stride)
+        out, tp, _ = gpu_forward_adjoint(nb, torch, net, z, s, gY, gE, gT9, stride=stride,
+                                         kernel=kernel)
         for k in ("dl", "dY0", "dT0", "Y"):
             assert np.array_equal(out[k], ref[k]), (stride, k)
     # the tape's records: the schedule and the kept states agree with the
