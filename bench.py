@@ -269,22 +269,24 @@ def run_native(args):
             torch.cuda.synchronize()
 
     if (args.blocks_per_sm or args.threads_per_block or args.ws_in_shared >= 0 or args.no_autotune
-            or args.specialize is not None):
+            or args.specialize is not None or args.kernel != "persistent"):
         launch = dict(blocks_per_sm=args.blocks_per_sm,
                       threads_per_block=args.threads_per_block,
                       ws_in_shared=args.ws_in_shared,
                       specialize=0 if args.specialize is None else args.specialize)
+        if args.kernel != "persistent":
+            launch["kernel"] = args.kernel
         tune_ms = None
     else:
         from paper_2312_02836_gb300.autotune import autotune
         launch = autotune(netc, Y0, T9, rho, s["t_end"], s["rtol"], s["atol"], extra=zk)
         tune_ms = launch.pop("_timings_ms")
 
-    def step(kernel="persistent"):
+    def step(kernel=None):
         nonlocal out
-        opts = launch if kernel == "persistent" else {}
-        out = nb.burn(netc, Y0, T9, rho, s["t_end"], s["rtol"], s["atol"],
-                      kernel=kernel, out=out, **opts, **zk)
+        opts = dict(launch) if kernel is None else dict(kernel=kernel)
+        out = nb.burn(netc, Y0, T9, rho, s["t_end"], s["rtol"], s["atol"], out=out,
+                      **opts, **zk)
 
     for _ in range(args.warmup):
         step()
@@ -303,7 +305,8 @@ def run_native(args):
     ms = [a.elapsed_time(b) for a, b in ev]
     mean_ms = max_over_ranks(statistics.mean(ms), dev)
     variant = netc.info()["last_specialized"]
-    kname = "nb_spec_burn" if variant else "k_burn_persistent"
+    kname = ("k_burn_coop" if launch.get("kernel") == "coop" else
+             "nb_spec_burn" if variant else "k_burn_persistent")
     counters = out.counters.cpu().numpy()
     status = out.status.cpu().numpy()
     ops = metrics.burn_ops(info, counters, net_spec.self_heating)
@@ -389,7 +392,9 @@ def run_native(args):
             "config": {"workload": WORKLOAD_DESC if workload == WORKLOAD else
                        workload_desc(workload, Z), "zones_per_gpu": Z,
                        "l2": "256 MiB buffer written between timed steps (L2 flush)",
-                       "kernel": ("persistent lane-per-zone, device work queue, "
+                       "kernel": ("persistent warp-per-zone, device work queue, arrays in "
+                                  "shared memory" if launch.get("kernel") == "coop" else
+                                  "persistent lane-per-zone, device work queue, "
                                   + ("code generated for the network (storage variant %d)" % variant
                                      if variant else "generic network walk")),
                        "launch": launch,
@@ -660,6 +665,9 @@ def main():
     p.add_argument("--ws-in-shared", type=int, default=-1)
     p.add_argument("--specialize", type=int, default=None,
                    help="-1 generic kernel, 0 automatic, 1..3 specialised variant")
+    p.add_argument("--kernel", default="persistent", choices=["persistent", "coop"],
+                   help="the main workload's kernel (coop: one warp per zone); "
+                        "persistent lets the autotuner choose")
     p.add_argument("--cpu-zones", type=int, default=8192)
     p.add_argument("--ref-zones", type=int, default=4096)
     p.add_argument("--no-cpu-baseline", action="store_true")

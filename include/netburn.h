@@ -202,6 +202,7 @@ typedef struct {
                                NB_Z_NONFINITE. */
 } nb_options;
 
+#define NB_KERNEL_AUTO (-1)     /* adjoint only: the choice made for opt NULL */
 #define NB_KERNEL_PERSISTENT 0  /* lane-per-zone, device work queue */
 #define NB_KERNEL_PLAIN 1       /* one thread per zone, no queue */
 #define NB_KERNEL_COOP 2        /* warp-per-zone, device work queue: the
@@ -307,10 +308,17 @@ int nb_tape_read(void* tape, int64_t z, int32_t cap, double* t, double* h,
 int nb_burn_adjoint(nb_net net, void* tape, int32_t K, const double* gY,
                     const double* gE, const double* gT9, double* d_ln_mult,
                     double* dY0, double* dT0, void* stream);
-/* nb_burn_adjoint with launch options (opt NULL: as nb_burn_adjoint, which
- * runs one warp per zone for networks of 24 or more state entries and one
- * lane per zone below).  From opt: kernel (NB_KERNEL_PERSISTENT one lane per
- * zone, NB_KERNEL_COOP one warp per zone), threads_per_block (lane kernel at
+/* nb_burn_adjoint with launch options (opt NULL, or opt->kernel
+ * NB_KERNEL_AUTO: as nb_burn_adjoint, which on a tape with checkpoint stride
+ * above 1 recomputes in the arithmetic of the burn that recorded it (one
+ * lane per zone after NB_KERNEL_PERSISTENT or NB_KERNEL_PLAIN, one warp per
+ * zone after NB_KERNEL_COOP), and at stride 1 runs one warp per zone for
+ * networks of 24 or more state entries and one lane per zone below).  From
+ * opt: kernel (NB_KERNEL_PERSISTENT one lane per zone, NB_KERNEL_COOP one
+ * warp per zone; at stride above 1 it must be the recording burn's family,
+ * else NB_E_TAPE, because the other family's arithmetic would recompute
+ * states that differ from the recorded burn's in the last bits),
+ * threads_per_block (lane kernel at
  * most 128; warp kernel: warps per block x 32, at most 256, default as many
  * as fit in shared memory up to 4), blocks_per_sm, ws_in_shared (0: the
  * warp kernel keeps its arrays in global memory) and blob_in_shared (0: the

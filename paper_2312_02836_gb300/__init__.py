@@ -159,8 +159,8 @@ def _options(kernel, threads_per_block, blocks_per_sm, blob_in_shared,
     o = _abi.Options()
     _abi.load().nb_default_options(C.byref(o))
     if isinstance(kernel, str):
-        kernel = {"persistent": KERNEL_PERSISTENT, "plain": KERNEL_PLAIN,
-                  "coop": KERNEL_COOP}[kernel]
+        kernel = {"auto": _abi.KERNEL_AUTO, "persistent": KERNEL_PERSISTENT,
+                  "plain": KERNEL_PLAIN, "coop": KERNEL_COOP}[kernel]
     o.kernel = int(kernel)
     o.threads_per_block = int(threads_per_block)
     o.blocks_per_sm = int(blocks_per_sm)
@@ -449,9 +449,12 @@ def adjoint(net: Network, tape: Tape, gY, gE=None, gT9=None, *, stream=None,
             want_initial=True, kernel="auto", threads_per_block=0, blocks_per_sm=0,
             ws_in_shared=-1, blob_in_shared=-1):
     """Discrete adjoint of the burn recorded on ``tape``.  gY [K,Z,N], gE and
-    gT9 [K,Z] (or None).  kernel: "auto" (one warp per zone for networks of
-    24 or more state entries), "persistent" (one lane per zone) or "coop".
-    Returns (d_ln_mult [K,Z,R], dY0 [K,Z,N], dT0 [K,Z])."""
+    gT9 [K,Z] (or None).  kernel: "auto" (on a checkpointed tape the
+    arithmetic of the burn that recorded it; at stride 1 one warp per zone
+    for networks of 24 or more state entries), "persistent" (one lane per
+    zone) or "coop" (one warp per zone); on a checkpointed tape an explicit
+    kernel must match the recording burn's.  Returns (d_ln_mult [K,Z,R],
+    dY0 [K,Z,N], dT0 [K,Z])."""
     torch = _torch()
     if tape.recorded is None:
         raise NetburnError("tape holds no burn")
@@ -473,7 +476,8 @@ def adjoint(net: Network, tape: Tape, gY, gE=None, gT9=None, *, stream=None,
     st = stream if stream is not None else torch.cuda.current_stream(dev)
     ptr = lambda t: None if t is None else t.data_ptr()
     o = None
-    if kernel != "auto":
+    if (kernel, threads_per_block, blocks_per_sm, ws_in_shared, blob_in_shared) != \
+            ("auto", 0, 0, -1, -1):
         o = _options(kernel, threads_per_block, blocks_per_sm, blob_in_shared, 500000,
                      ws_in_shared)
     rc = _abi.load().nb_burn_adjoint_ex(net.handle, tape.handle, K, ptr(gY), ptr(gE),

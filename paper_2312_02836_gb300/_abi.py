@@ -18,6 +18,7 @@ ZONE_STATUS = {0: "OK", 1: "MAX_STEPS", 2: "DT_UNDERFLOW", 3: "NEWTON_FAIL",
 NCOUNT = 8
 COUNTER_NAMES = ("accepted", "rejected_error", "rejected_newton", "newton_iters",
                  "jacobians", "rhs_evals", "rate_evals", "edot_evals")
+KERNEL_AUTO = -1
 KERNEL_PERSISTENT = 0
 KERNEL_PLAIN = 1
 KERNEL_COOP = 2

@@ -199,9 +199,15 @@ extern "C" int nb_burn_adjoint_ex(nb_net net, void* tape, int32_t K, const doubl
   nb_options o;
   nb_default_options(&o);
   if (opt) o = *opt;
-  // the kernel: as asked, else one warp per zone from 24 state entries on
-  int kernel = opt ? o.kernel : (n >= 24 ? NB_KERNEL_COOP : NB_KERNEL_PERSISTENT);
+  // the kernel: as asked; else, when blocks are recomputed (stride > 1), the
+  // arithmetic of the recording burn, so that the recomputed states are the
+  // forward's bits; else one warp per zone from 24 state entries on
+  int kernel = o.kernel;
+  if (!opt || kernel == NB_KERNEL_AUTO)
+    kernel = tp->dev.stride > 1 ? tp->family
+                                : (n >= 24 ? NB_KERNEL_COOP : NB_KERNEL_PERSISTENT);
   if (kernel != NB_KERNEL_COOP && kernel != NB_KERNEL_PERSISTENT) return NB_E_ARG;
+  if (tp->dev.stride > 1 && kernel != tp->family) return NB_E_TAPE;
   cudaStream_t st = (cudaStream_t)stream;
   std::lock_guard<std::mutex> lk(net->mu);
   const size_t blob_b = (size_t)h.bytes;

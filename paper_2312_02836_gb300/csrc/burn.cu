@@ -447,6 +447,9 @@ static int launch_coop(nb_net net, BurnParams& P, const nb_options& o, cudaStrea
 static int launch_burn(nb_net net, BurnParams& P, const nb_options& o,
                        cudaStream_t st) {
   net->last_spec = 0;
+  if (o.kernel != NB_KERNEL_PERSISTENT && o.kernel != NB_KERNEL_PLAIN &&
+      o.kernel != NB_KERNEL_COOP)
+    return NB_E_ARG;
   int tpb = o.threads_per_block > 0 ? o.threads_per_block : 128;
   if (o.threads_per_block <= 0 && o.kernel != NB_KERNEL_PLAIN) {
     // few zones: smaller blocks, so that every SM gets some
@@ -624,22 +627,26 @@ extern "C" int nb_burn_batch(nb_net net, int64_t Z, const double* Y0, const doub
   P.zeta_zone = o.zeta_zone;
   cudaStream_t st = (cudaStream_t)stream;
   std::lock_guard<std::mutex> lk(net->mu);
-  if (tape) {
-    nb_tape_s* tp = (nb_tape_s*)tape;
+  nb_tape_s* tp = (nb_tape_s*)tape;
+  if (tp) {
     if (tp->magic != 0x7a9e5eedu || tp->net != net || tp->Z < Z) return NB_E_TAPE;
     P.use_tape = 1;
     P.tape = tp->dev;
-    tp->recZ = Z;
-    tp->recorded = 1;
-    tp->t_end = t_end; tp->rtol = rtol; tp->atol = atol;
-    tp->has_lnm = ln_mult != nullptr;
-    tp->lnm_per_zone = P.lnm_per_zone;
+    tp->recorded = 0;
     if (ln_mult) {
       const size_t cnt = (size_t)(P.lnm_per_zone ? Z : 1) * net->h.R;
       CK(cudaMemcpyAsync(tp->lnm, ln_mult, cnt * sizeof(double), cudaMemcpyDeviceToDevice, st));
     }
   }
-  return launch_burn(net, P, o, st);
+  rc = launch_burn(net, P, o, st);
+  if (rc || !tp) return rc;
+  tp->recZ = Z;
+  tp->recorded = 1;
+  tp->family = o.kernel == NB_KERNEL_COOP ? NB_KERNEL_COOP : NB_KERNEL_PERSISTENT;
+  tp->t_end = t_end; tp->rtol = rtol; tp->atol = atol;
+  tp->has_lnm = ln_mult != nullptr;
+  tp->lnm_per_zone = P.lnm_per_zone;
+  return NB_OK;
 }
 
 extern "C" int nb_burn_batch_host(nb_net net, int64_t Z, const double* Y0,

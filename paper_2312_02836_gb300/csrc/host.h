@@ -52,6 +52,10 @@ struct nb_tape_s {
   int has_lnm = 0;
   double t_end = 0, rtol = 0, atol = 0;
   int recorded = 0;
+  // arithmetic of the recording burn: NB_KERNEL_PERSISTENT for the
+  // one-zone-per-lane kernels (which share their bits), NB_KERNEL_COOP for
+  // one zone per warp; a checkpointed block is recomputed in the same one
+  int family = 0;
   unsigned magic = 0x7a9e5eedu;
 };
 

@@ -31,7 +31,9 @@ def nb_mod():
 def gpu_forward_adjoint(nb, torch, net, z, s, gY, gE, gT9, ln_mult=None, max_steps=6000,
                         stride=1, kernel="auto"):
     """Forward with a tape, then the adjoint; returns the adjoint outputs,
-    the forward outputs and the tape."""
+    the forward outputs and the tape.  The forward runs in the adjoint
+    kernel's arithmetic (one warp per zone for "coop", one lane per zone
+    otherwise), which a checkpointed tape requires."""
     dev = torch.device("cuda")
     Z = z["T9"].shape[0]
     nc = nb.Network(net)
@@ -39,7 +41,8 @@ def gpu_forward_adjoint(nb, torch, net, z, s, gY, gE, gT9, ln_mult=None, max_ste
     lm = None if ln_mult is None else torch.from_numpy(np.ascontiguousarray(ln_mult)).to(dev)
     fw = nb.burn(nc, torch.from_numpy(z["Y"]).to(dev), torch.from_numpy(z["T9"]).to(dev),
                  torch.from_numpy(z["rho"]).to(dev), s["t_end"], s["rtol"], s["atol"], lm,
-                 tape=tape, zeta=torch.from_numpy(z["zeta"]).to(dev) if "zeta" in z else None)
+                 tape=tape, zeta=torch.from_numpy(z["zeta"]).to(dev) if "zeta" in z else None,
+                 kernel="coop" if kernel == "coop" else "persistent")
     t = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     dl, dY0, dT0 = nb.adjoint(nc, tape, t(gY), t(gE), t(gT9), kernel=kernel)
     torch.cuda.synchronize()
@@ -107,6 +110,32 @@ def test_checkpointed_tape_gives_the_full_tape_bits(name, Z, kernel):
         assert len(full["t"]) == ref["counters"][i, 0] + 1
         np.testing.assert_array_equal(full["x"][-1, :net.N], ref["Y"][i])
         np.testing.assert_array_equal(full["x"][0, :net.N], z["Y"][i])
+
+
+def test_checkpointed_tape_recomputes_in_the_recording_arithmetic():
+    # a checkpointed block is recomputed by the kernel family that recorded
+    # it: "auto" follows the tape, the other family is refused, and at
+    # stride 1 (nothing recomputed) either family reads the tape
+    nb, torch = nb_mod()
+    net, z, s = gen.problem("net48_adjoint", 8)
+    dev = torch.device("cuda")
+    nc = nb.Network(net)
+    gY = torch.from_numpy(np.random.default_rng(2).normal(size=(1, 8, net.N))).to(dev)
+    args = [torch.from_numpy(z[k]).to(dev) for k in ("Y", "T9", "rho")]
+    for fwk, other in (("persistent", "coop"), ("coop", "persistent")):
+        tape = nb.Tape(nc, 8, 4000, 16)
+        nb.burn(nc, *args, s["t_end"], s["rtol"], s["atol"], tape=tape, kernel=fwk)
+        a = nb.adjoint(nc, tape, gY, kernel="auto")[0]
+        b = nb.adjoint(nc, tape, gY, kernel=fwk)[0]
+        assert torch.equal(a, b)
+        with pytest.raises(nb.NetburnError):
+            nb.adjoint(nc, tape, gY, kernel=other)
+        tape1 = nb.Tape(nc, 8, 4000, 1)
+        nb.burn(nc, *args, s["t_end"], s["rtol"], s["atol"], tape=tape1, kernel=fwk)
+        c = nb.adjoint(nc, tape1, gY, kernel=fwk)[0]
+        d = nb.adjoint(nc, tape1, gY, kernel=other)[0]
+        assert torch.equal(a, c)
+        assert torch.allclose(c, d, rtol=1e-7, atol=1e-10 * float(c.abs().max()))
 
 
 def test_dot_product_identity():
