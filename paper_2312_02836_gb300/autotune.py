@@ -53,6 +53,18 @@ COOP_CANDIDATES = (
 DEFAULT_CANDIDATES = GENERIC_CANDIDATES + SPECIALIZED_CANDIDATES + COOP_CANDIDATES
 
 
+def eligible(info: dict, candidates=DEFAULT_CANDIDATES) -> list:
+    """The candidates worth timing for a network (``Network.info()``)."""
+    out = list(candidates)
+    if not info["specialize_auto"]:
+        # no generated kernel for this network: the generic and warp kernels
+        out = [c for c in out if c.get("kernel") == "coop" or c.get("specialize", 0) < 0]
+    if info["n_state"] < 24:
+        # a warp per zone leaves most lanes idle on a small network
+        out = [c for c in out if c.get("kernel") != "coop"]
+    return out
+
+
 def autotune(net, Y0, T9, rho, t_end, rtol, atol, ln_mult=None, *,
              candidates=DEFAULT_CANDIDATES, key: Optional[str] = None,
              verbose: bool = False, extra: Optional[dict] = None) -> dict:
@@ -70,12 +82,7 @@ def autotune(net, Y0, T9, rho, t_end, rtol, atol, ln_mult=None, *,
     stream = torch.cuda.current_stream(dev)
     best, best_ms, timings = None, float("inf"), []
     out = None
-    info = net.info()
-    if not info["specialize_auto"]:
-        candidates = [c for c in candidates if c.get("specialize", 0) < 0]
-    if info["n_state"] < 24:
-        # a warp per zone leaves most lanes idle on a small network
-        candidates = [c for c in candidates if c.get("kernel") != "coop"]
+    candidates = eligible(net.info(), candidates)
     for cand in candidates:
         try:
             out = burn(net, Y0, T9, rho, t_end, rtol, atol, ln_mult, out=out, **cand, **extra)

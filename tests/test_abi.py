@@ -97,3 +97,14 @@ def test_multi_network_argument_checks_on_host():
     assert lib.nb_burn_multi(1, None, 1.0, 1e-8, 1e-12, None, None) == -1
     assert lib.nb_burn_multi(1, sets, 1.0, -1e-8, 1e-12, None, None) == -1
     assert lib.nb_burn_multi(1, sets, float("nan"), 1e-8, 1e-12, None, None) == -1
+
+
+def test_autotune_candidates_per_network():
+    from paper_2312_02836_gb300.autotune import (COOP_CANDIDATES, GENERIC_CANDIDATES,
+                                                 SPECIALIZED_CANDIDATES, eligible)
+    # a large network with no generated kernel: generic lane and warp kernels
+    big = eligible(dict(specialize_auto=False, n_state=48))
+    assert big == list(GENERIC_CANDIDATES) + list(COOP_CANDIDATES)
+    # a small network that has one: lane kernels only, generated ones included
+    small = eligible(dict(specialize_auto=True, n_state=14))
+    assert small == list(GENERIC_CANDIDATES) + list(SPECIALIZED_CANDIDATES)
