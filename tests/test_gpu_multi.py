@@ -1,11 +1,14 @@
 """Several networks in one launch (nb_burn_multi): every set's zones must
 come out bit for bit as a single-network burn of the same zones gives them
 (the generic kernel, and so the specialised one too), whatever sets share
-the launch.  Parity of those burns with the oracle is the parity tests'."""
+the launch; and each set's zones meet the parity bar against the oracle
+directly."""
 import numpy as np
 import pytest
 
 import gen
+import oracle
+from tests.parity import compare, oracle_spread, to_numpy
 
 pytestmark = pytest.mark.gpu
 
@@ -99,3 +102,34 @@ def test_multi_network_batch_with_screening_and_tables():
         torch.cuda.synchronize()
         assert int((out.status == 0).sum()) == d["Y0"].shape[0]
         _equal(out, ref)
+
+
+def test_multi_network_batch_against_oracle():
+    # one launch over four networks (fixed T, self-heating, screened, 48
+    # species at its own end time per zone), each set held to the oracle
+    nb, torch = _mods()
+    cases = (("chain13_heat", 512), ("net48", 64), ("chain13", 256), ("chain13_heat_scr", 256))
+    sets, probs = [], []
+    for name, Z in cases:
+        d, net, s = _set(nb, torch, name, Z)
+        z = gen.problem(name, Z)[1]
+        if "zeta" in z:
+            d["zeta"] = torch.from_numpy(z["zeta"]).cuda()
+        sets.append(d)
+        probs.append((net, z, s))
+    s0 = probs[0][2]
+    for d, (net, z, s) in zip(sets, probs):
+        assert (s["rtol"], s["atol"]) == (s0["rtol"], s0["atol"])
+        if s["t_end"] != s0["t_end"]:
+            d["t_end"] = torch.full((z["T9"].shape[0],), s["t_end"], dtype=torch.float64,
+                                    device="cuda")
+    outs = nb.burn_multi(sets, s0["t_end"], s0["rtol"], s0["atol"])
+    torch.cuda.synchronize()
+    for (name, Z), (net, z, s), out in zip(cases, probs, outs):
+        run = lambda v: oracle.burn(net, z["Y"], z["T9"], z["rho"], s["t_end"], s["rtol"],
+                                    s["atol"], zeta=z.get("zeta"), variant=v)
+        o = run(0)
+        spread = oracle_spread(o, [run(v) for v in oracle.VARIANTS], s["atol"], s["rtol"])
+        rep = compare(to_numpy(out), o, s["atol"], rtol=s["rtol"], spread=spread)
+        assert (to_numpy(out)["status"] == 0).all()
+        print(name, rep)
