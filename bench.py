@@ -146,9 +146,9 @@ class Clocks:
 
 
 def zone_bytes(N: int) -> int:
-    """Algorithmic HBM bytes per zone-burn: Y0, T9, rho in; Y, T9, E, eight
+    """Algorithmic HBM bytes per zone-burn: Y0, T9, rho in; Y, T9, E, nine
     int32 counters and the status out."""
-    return 16 * N + 8 * 4 + 8 * 4 + 4
+    return 16 * N + 8 * 4 + 9 * 4 + 4
 
 
 def workload_desc(name: str, Z: int) -> str:
@@ -322,7 +322,7 @@ def run_native(args):
     hout = dict(Y=torch.empty((Z, N), dtype=torch.float64).pin_memory().numpy(),
                 T9=torch.empty(Z, dtype=torch.float64).pin_memory().numpy(),
                 E=torch.empty(Z, dtype=torch.float64).pin_memory().numpy(),
-                counters=torch.empty((Z, 8), dtype=torch.int32).pin_memory().numpy(),
+                counters=torch.empty((Z, nb.NCOUNT), dtype=torch.int32).pin_memory().numpy(),
                 status=torch.empty(Z, dtype=torch.int32).pin_memory().numpy())
     if not args.no_e2e:
         nb.burn_host(netc, hY0, hT9, hrho, s["t_end"], s["rtol"], s["atol"], out=hout,

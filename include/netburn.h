@@ -72,7 +72,7 @@ extern "C" {
                                 that lost more than 40 bits to cancellation */
 
 /* per-zone counters, counters[z * NB_NCOUNT + c] */
-#define NB_NCOUNT 8
+#define NB_NCOUNT 9
 #define NB_C_ACCEPTED 0
 #define NB_C_REJ_ERROR 1
 #define NB_C_REJ_NEWTON 2
@@ -81,6 +81,9 @@ extern "C" {
 #define NB_C_RHS 5
 #define NB_C_RATE_EVALS 6    /* evaluations of all lambda_r(T9) */
 #define NB_C_EDOT 7          /* energy-only evaluations for E */
+#define NB_C_ORDER_SUM 8     /* sum of the BDF orders of the accepted steps: with
+                                the counts above, a fingerprint of the path the
+                                step and order control took */
 
 #ifndef __CUDACC_RTC__ /* the run-time compiled kernels need only the codes above */
 typedef struct nb_net_s* nb_net;

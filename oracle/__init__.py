@@ -26,9 +26,9 @@ _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-N_COUNTERS = 8
+N_COUNTERS = 9
 COUNTER_NAMES = ("accepted", "rejected_error", "rejected_newton", "newton_iters",
-                 "jacobians", "rhs_evals", "rate_evals", "edot_evals")
+                 "jacobians", "rhs_evals", "rate_evals", "edot_evals", "order_sum")
 STATUS = {0: "OK", 1: "MAX_STEPS", 2: "DT_UNDERFLOW", 3: "NEWTON_FAIL",
           5: "NONFINITE", 7: "SINGULAR"}
 

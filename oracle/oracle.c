@@ -107,7 +107,7 @@ enum { ST_OK = 0, ST_MAX_STEPS = 1, ST_DT_UNDERFLOW = 2, ST_NEWTON_FAIL = 3,
 
 /* per-zone event counters */
 enum { C_ACC = 0, C_REJ_ERR, C_REJ_NEWTON, C_NEWTON_IT, C_JAC, C_RHS, C_TEVAL,
-       C_EDOT, C_COUNT };
+       C_EDOT, C_ORDSUM, C_COUNT };   /* C_ORDSUM: sum of the accepted steps' orders */
 
 typedef struct {
     int32_t N, R, self_heating;
@@ -867,6 +867,7 @@ static int burn_zone(const ora_network* net, const ora_options* opt,
         t = t_new;
         E = E_new;
         cnt[C_ACC]++;
+        cnt[C_ORDSUM] += kk;
         if (tape && tape->count < tape->cap) {
             int s = tape->count++;
             tape->t[s] = t; tape->k[s] = kk; tape->E[s] = E;

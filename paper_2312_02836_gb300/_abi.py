@@ -15,9 +15,9 @@ ERRORS = {-1: "NB_E_ARG", -2: "NB_E_TOPOLOGY", -3: "NB_E_TOO_LARGE",
           -4: "NB_E_CUDA", -5: "NB_E_NOMEM", -6: "NB_E_TAPE", -7: "NB_E_COMPILE"}
 ZONE_STATUS = {0: "OK", 1: "MAX_STEPS", 2: "DT_UNDERFLOW", 3: "NEWTON_FAIL",
                4: "TAPE_FULL", 5: "NONFINITE", 6: "TIMEOUT", 7: "SINGULAR"}
-NCOUNT = 8
+NCOUNT = 9
 COUNTER_NAMES = ("accepted", "rejected_error", "rejected_newton", "newton_iters",
-                 "jacobians", "rhs_evals", "rate_evals", "edot_evals")
+                 "jacobians", "rhs_evals", "rate_evals", "edot_evals", "order_sum")
 KERNEL_AUTO = -1
 KERNEL_PERSISTENT = 0
 KERNEL_PLAIN = 1

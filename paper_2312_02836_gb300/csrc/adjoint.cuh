@@ -164,7 +164,7 @@ NB_HD inline bool adj_init(const NT& t, AdjZone& Zs, WT& w, const AT& a, const A
   s.E = 0.0;
   s.k = 1;
   s.c_acc = s.c_rej_err = s.c_rej_newton = s.c_newton = 0;
-  s.c_jac = s.c_rhs = s.c_teval = s.c_edot = 0;
+  s.c_jac = s.c_rhs = s.c_teval = s.c_edot = s.c_ordsum = 0;
   tab_zone(t, s, state_ptr(n, A, z, 0));   // the recorded initial state
   s.lnm = A.lnm ? (A.lnm_per_zone ? A.lnm + (size_t)z * t.R : A.lnm) : nullptr;
   // fixed temperature: the rates of the whole burn (with their T9 slopes)

@@ -14,11 +14,11 @@ namespace nb {
 
 constexpr int HMAX = 7;       // accepted points kept per zone
 constexpr int KMAX = 5;       // highest BDF order
-constexpr int NCOUNT = 8;     // per-zone event counters
+constexpr int NCOUNT = 9;     // per-zone event counters
 constexpr int WS_LANES = 32;  // per-lane workspace is interleaved by warp lane
 
 enum Counter { C_ACC = 0, C_REJ_ERR, C_REJ_NEWTON, C_NEWTON_IT, C_JAC, C_RHS,
-               C_TEVAL, C_EDOT };
+               C_TEVAL, C_EDOT, C_ORDSUM };
 
 // Jacobian slot flags
 enum : uint8_t { SLOT_DIAG = 1, SLOT_TROW = 2, SLOT_TT = 4 };

@@ -155,7 +155,7 @@ struct Zone {
   double tab_u;               // and the weight within it
   const double* lnm;
   int k, nh, hh, nconsec, nfail, status;
-  int c_acc, c_rej_err, c_rej_newton, c_newton, c_jac, c_rhs, c_teval, c_edot;
+  int c_acc, c_rej_err, c_rej_newton, c_newton, c_jac, c_rhs, c_teval, c_edot, c_ordsum;
 };
 
 NB_HD __forceinline__ int hslot(const Zone& s, int j) {
@@ -598,7 +598,7 @@ NB_HD __forceinline__ bool zone_init(const NT& t, Zone& s, WT& w, const BurnPara
   s.t = 0.0; s.E = 0.0; s.k = 1; s.nh = 1; s.hh = 0; s.nconsec = 0; s.nfail = 0;
   s.status = NB_Z_OK;
   s.c_acc = s.c_rej_err = s.c_rej_newton = s.c_newton = 0;
-  s.c_jac = s.c_rhs = s.c_teval = s.c_edot = 0;
+  s.c_jac = s.c_rhs = s.c_teval = s.c_edot = s.c_ordsum = 0;
   s.T9f = P.T9_0[z];
   s.rho = P.rho[z];
   s.rho2 = s.rho * s.rho;
@@ -850,6 +850,7 @@ NB_HD __forceinline__ bool zone_attempt(const NT& t, Zone& s, WT& w, const BurnP
   s.t = t_new;
   s.E = E_new;
   s.c_acc++;
+  s.c_ordsum += kk;
   if (!tape_record(t, P, s, w.x, h, kk)) { s.status = NB_Z_TAPE_FULL; return true; }
   if (s.t >= s.tend) { s.h = h; return true; }
   // next step size and order
@@ -952,7 +953,7 @@ NB_HD __forceinline__ void zone_finish(const NT& t, const Zone& s, const WT& w,
     int32_t* c = P.counters + (unsigned long long)z * NCOUNT;
     c[C_ACC] = s.c_acc; c[C_REJ_ERR] = s.c_rej_err; c[C_REJ_NEWTON] = s.c_rej_newton;
     c[C_NEWTON_IT] = s.c_newton; c[C_JAC] = s.c_jac; c[C_RHS] = s.c_rhs;
-    c[C_TEVAL] = s.c_teval; c[C_EDOT] = s.c_edot;
+    c[C_TEVAL] = s.c_teval; c[C_EDOT] = s.c_edot; c[C_ORDSUM] = s.c_ordsum;
   }
 }
 

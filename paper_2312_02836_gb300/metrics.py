@@ -19,8 +19,9 @@ FP64_PEAK_TFLOPS = SM_COUNT * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12
 
 def burn_ops(info: dict, counters: np.ndarray, self_heating: bool) -> dict:
     """Totals over the zones of one burn: flops and special functions."""
-    c = np.asarray(counters, dtype=np.int64).reshape(-1, 8).sum(0)
-    acc, rej_e, rej_n, newton, jac, rhs, teval, edot = (int(v) for v in c)
+    counters = np.asarray(counters, dtype=np.int64)
+    c = counters.reshape(-1, counters.shape[-1]).sum(0)
+    acc, rej_e, rej_n, newton, jac, rhs, teval, edot = (int(v) for v in c[:8])
     attempts = acc + rej_e + rej_n
     n = info["n_state"]
     R = info["n_reactions"]

@@ -15,9 +15,14 @@ how far it lands from the oracle is the oracle's own rounding noise on that
 very workload.  An entry that misses the target bar passes only when its
 deviation is within twice that measured noise:
 
-  * a zone took the oracle's path when all eight of its counters (accepted
+  * a zone took the oracle's path when all nine of its counters (accepted
     and rejected steps, Newton iterations, Jacobians, right-hand sides,
-    rate and energy evaluations) equal the oracle's;
+    rate and energy evaluations, the sum of the accepted steps' orders)
+    equal the oracle's.  An order choice can be decided by rounding: after
+    three steps of a slow 128-species zone the order-2 error estimate is
+    3.6e-7 w, its components 250 times the states' rounding, and the device
+    code takes order 2 where the oracle keeps order 1 (a 1.2e-7 change of E,
+    which is not in the error norm);
   * spread P = max over variants, zones and species of |Y_var - Y_ora| / w,
     w = atol + rtol |Y_ora| (the weight the method resolves a species to),
     over the zones where the variant took the oracle's path; every entry of

@@ -49,7 +49,7 @@ def host_run(lib, net, z, s, stride, gY, gE, gT9, cap=6000):
     arrays, topo, coef = _topology(net)
     scap = 1 + ((cap - 1 + stride - 1) // stride) * min(stride, 7)
     out = dict(Y=np.empty((Z, net.N)), T9=np.empty(Z), E=np.empty(Z),
-               counters=np.zeros((Z, 8), np.int32), status=np.zeros(Z, np.int32),
+               counters=np.zeros((Z, 9), np.int32), status=np.zeros(Z, np.int32),
                sched=np.zeros((Z, cap, 2)), ord=np.zeros((Z, cap), np.int8),
                states=np.full((Z, scap, n + 1), np.nan), steps=np.zeros(Z, np.int32),
                dl=np.zeros((K, Z, net.R)), dY0=np.zeros((K, Z, net.N)), dT0=np.zeros((K, Z)))

@@ -49,7 +49,7 @@ def test_host_integrator_matches_oracle(host_lib, name, Z):
     arrays, topo, coef = _topology(net)
     p = lambda a: None if a is None else a.ctypes.data
     Y = np.empty((Z, net.N)); T9 = np.empty(Z); E = np.empty(Z)
-    cnt = np.zeros((Z, 8), np.int32); st = np.zeros(Z, np.int32)
+    cnt = np.zeros((Z, 9), np.int32); st = np.zeros(Z, np.int32)
     zeta = z.get("zeta")
     rc = host_lib.host_burn(C.byref(topo), coef, Z, p(z["Y"]), p(z["T9"]), p(z["rho"]),
                             p(zeta), s["t_end"], s["rtol"], s["atol"],
