@@ -48,6 +48,9 @@ COOP_CANDIDATES = (
     dict(kernel="coop", threads_per_block=0, blocks_per_sm=0),
     dict(kernel="coop", threads_per_block=64, blocks_per_sm=0),
     dict(kernel="coop", threads_per_block=32, blocks_per_sm=0),
+    # one block of four warps per SM: less shared memory taken, more L1 left
+    # for the network's index lists
+    dict(kernel="coop", threads_per_block=128, blocks_per_sm=1),
 )
 
 DEFAULT_CANDIDATES = GENERIC_CANDIDATES + SPECIALIZED_CANDIDATES + COOP_CANDIDATES

@@ -245,7 +245,8 @@ std::string specialized_source(const std::vector<uint8_t>& blob, int variant) {
   o("NB_HD __forceinline__ void eval_rates_near(const GNet&, const Zone& s, GWS& w, double T9,"
     " const TPow& ref, double T9ref) {\n");
   if (sh) {
-    o("  const TPow p = t_powers(T9, false, s.scr);\n  const DPhi d = delta_phi(p, ref, T9, T9ref);\n"
+    o("  DPhi d;\n  TPow p;\n  bool have_p = !delta_phi_series(ref, T9, T9ref, d);\n"
+      "  if (have_p) {\n    p = t_powers(T9, false, s.scr);\n    d = delta_phi(p, ref, T9, T9ref);\n  }\n"
       "  const double* lnm = s.lnm;\n  double de, e;\n");
     if (has_tab) o("  const TCell tc = t_cell(NB_TAB_T9, %d, T9);\n  double dl;\n", h.tab_nt);
     // hot part: the small-delta updates, straight-line; a reaction whose
@@ -266,14 +267,19 @@ std::string specialized_source(const std::vector<uint8_t>& blob, int variant) {
         ++nbit;
       } else {
         o("  if (small_delta(de)) {\n    w.k[%d] = rate_near(w.kp[%d], de);\n  } else {\n", r, r);
+        o("    if (!have_p) {\n      p = t_powers(T9, false, s.scr);\n      have_p = true;\n    }\n");
         emit_full(r, "    ", false);
         o("  }\n");
       }
     }
+    bool always = false;
+    for (int r = 0; r < R; ++r) always = always || ap[r] >= 0 || (has_tab && tab_of[r] >= 0);
+    if (always) o("  if (!have_p) {\n    p = t_powers(T9, false, s.scr);\n    have_p = true;\n  }\n");
     for (int r = 0; r < R; ++r)
       if (ap[r] >= 0 || (has_tab && tab_of[r] >= 0)) emit_full(r, "  ", false);
     if (!marked.empty()) {
       o("  if (full) {\n");
+      o("    if (!have_p) p = t_powers(T9, false, s.scr);\n");
       for (size_t b = 0; b < marked.size(); ++b) {
         o("    if (full & (1ull << %zu)) {\n", b);
         emit_full(marked[b], "      ", false);
@@ -351,7 +357,7 @@ std::string specialized_source(const std::vector<uint8_t>& blob, int variant) {
   for (int k = 0; k < n; ++k) {
     const Pivot& p = piv[k];
     o("  {\n    const double pv = w.lu[%d];\n    ok = ok && pivot_kept(pv, a%d);\n"
-      "    const double inv = 1.0 / pv;\n    w.lu[%d] = inv;\n", p.dslot, k, p.dslot);
+      "    const double inv = recip2(pv);\n    w.lu[%d] = inv;\n", p.dslot, k, p.dslot);
     const int nu = p.uend - p.ubeg;
     int dpos = p.dbeg;
     for (int li = p.lbeg; li < p.lend; ++li) {

@@ -125,17 +125,27 @@ __device__ __forceinline__ void eval_rates_near(const WNet& t, const Zone& s, co
                                                 double T9, const TPow& ref, double T9ref) {
   __syncwarp();
   const Net& g = t.g;
-  const TPow p = t_powers(T9, false, s.scr);
-  const DPhi d = delta_phi(p, ref, T9, T9ref);
+  DPhi d;
+  TPow p;
+  bool have_p = !delta_phi_series(ref, T9, T9ref, d);
+  if (have_p) {
+    p = t_powers(T9, false, s.scr);
+    d = delta_phi(p, ref, T9, T9ref);
+  }
   const TCell tc = g.tab_of ? t_cell(g.tab_t9, g.tab_nt, T9) : TCell{0, 0.0, 1.0, false};
   for (int r = t.lane; r < t.R; r += 32) {
     const double* a = g.coef + 7 * r;
     double de = rate_delta(a[1], a[2], a[3], a[4], a[5], a[6], d);
     if (g.scr) de = fma(g.scr[r], d.d7, de);
-    if (g.ap[r] < 0 && !(g.tab_of && g.tab_of[r] >= 0) && small_delta(de))
+    if (g.ap[r] < 0 && !(g.tab_of && g.tab_of[r] >= 0) && small_delta(de)) {
       w.k[r] = rate_near(w.kp[r], de);
-    else
+    } else {
+      if (!have_p) {
+        p = t_powers(T9, false, s.scr);
+        have_p = true;
+      }
       w.k[r] = rate_full(g, s, r, p, T9, tc, nullptr);
+    }
   }
   __syncwarp();
 }
@@ -239,7 +249,7 @@ __device__ __forceinline__ bool factor_M(const WNet& t, const CWS& w) {
     const Pivot p = g.piv[k];
     const double pv = w.lu[p.dslot];
     ok = ok && pivot_kept(pv, w.tmp[k]);
-    const double inv = 1.0 / pv;
+    const double inv = recip2(pv);
     const int nl = p.lend - p.lbeg, nu = p.uend - p.ubeg;
     for (int li = p.lbeg + t.lane; li < p.lend; li += 32) {
       const int ls = g.lslot[li];

@@ -209,8 +209,15 @@ NB_HD inline void eval_rates(const Net& t, const Zone& s, const WS& w, const TPo
 // Effective (alpha,p)(p,gamma) rates always take the full evaluation.
 NB_HD inline void eval_rates_near(const Net& t, const Zone& s, const WS& w, double T9,
                                   const TPow& ref, double T9ref) {
-  const TPow p = t_powers(T9, false, s.scr);
-  const DPhi d = delta_phi(p, ref, T9, T9ref);
+  // the changes of the powers by their series when T9 is close to the
+  // reference; the powers themselves only when a rate needs them
+  DPhi d;
+  TPow p;
+  bool have_p = !delta_phi_series(ref, T9, T9ref, d);
+  if (have_p) {
+    p = t_powers(T9, false, s.scr);
+    d = delta_phi(p, ref, T9, T9ref);
+  }
   const TCell tc = t.tab_of ? t_cell(t.tab_t9, t.tab_nt, T9) : TCell{0, 0.0, 1.0, false};
 #pragma unroll 2
   for (int r = 0; r < t.R; ++r) {
@@ -218,10 +225,15 @@ NB_HD inline void eval_rates_near(const Net& t, const Zone& s, const WS& w, doub
     double de = rate_delta(a[1], a[2], a[3], a[4], a[5], a[6], d);
     if (t.scr) de = fma(t.scr[r], d.d7, de);
     // tabulated and effective rates always take the full evaluation
-    if (t.ap[r] < 0 && !(t.tab_of && t.tab_of[r] >= 0) && small_delta(de))
+    if (t.ap[r] < 0 && !(t.tab_of && t.tab_of[r] >= 0) && small_delta(de)) {
       w.k[r] = rate_near(w.kp[r], de);
-    else
+    } else {
+      if (!have_p) {
+        p = t_powers(T9, false, s.scr);
+        have_p = true;
+      }
       w.k[r] = rate_full(t, s, r, p, T9, tc, nullptr);
+    }
   }
 }
 
@@ -326,7 +338,7 @@ NB_HD inline bool factor_M(const Net& t, const WS& w) {
     const Pivot p = t.piv[k];
     const double pv = w.lu[p.dslot];
     ok = ok && pivot_kept(pv, w.tmp[k]);
-    const double inv = 1.0 / pv;
+    const double inv = recip2(pv);
     w.lu[p.dslot] = inv;
     const int nu = p.uend - p.ubeg;
     int dpos = p.dbeg;

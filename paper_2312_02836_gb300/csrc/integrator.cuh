@@ -193,6 +193,40 @@ NB_HD __forceinline__ bool pivot_kept(double u, double a) {
   return finite_nonzero(u) && eu + 40 >= ea;
 }
 
+// Reciprocals by Newton-Raphson iteration, y <- y + y (1 - a y), which
+// squares the relative error of y, from the approximate reciprocal
+// instruction (rcp.approx.ftz.f64) as the seed: two FMAs a step instead of a
+// full division.  Arguments whose exponent is 0 or >= 2^1021 (0, subnormal,
+// huge, inf, NaN) take the division.
+NB_HD __forceinline__ bool recip_plain(double a) {
+  const long long e = (dbits(a) >> 52) & 0x7ff;
+  return e == 0 || e >= 0x7fd;
+}
+// One step: about 2^-44 relative.  For the error weights 1/(atol + rtol |x|),
+// which only scale the norms the step control compares with 1e-3 and 1.
+NB_HD __forceinline__ double recip1(double a) {
+#ifdef __CUDA_ARCH__
+  if (recip_plain(a)) return 1.0 / a;
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(a));
+  return fma(y, fma(-a, y, 1.0), y);
+#else
+  return 1.0 / a;
+#endif
+}
+// Two steps: within about an ulp of 1/a.  For the LU pivots.
+NB_HD __forceinline__ double recip2(double a) {
+#ifdef __CUDA_ARCH__
+  if (recip_plain(a)) return 1.0 / a;
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(a));
+  y = fma(y, fma(-a, y, 1.0), y);
+  return fma(y, fma(-a, y, 1.0), y);
+#else
+  return 1.0 / a;
+#endif
+}
+
 // ---------------------------------------------------------------- model
 // pieces both network types share, so that their arithmetic is one text
 
@@ -351,6 +385,29 @@ NB_HD __forceinline__ DPhi delta_phi(const TPow& p, const TPow& r, double T9, do
   return d;
 }
 
+// The same differences from the relative change x = (T9 - T9r)/T9r when
+// |x| <= 2^-14, the case of every Newton iteration of an attempt: the
+// binomial and logarithm series of (1+x)^a - 1 and ln(1+x) to x^4, whose
+// first omitted term is below 2^-55 of the kept ones (more accurate than the
+// difference of the two rounded powers), with no cbrt, log or division.
+// False, and d untouched, for a larger change.
+NB_HD __forceinline__ double binom4(double x, double c1, double c2, double c3, double c4) {
+  return x * fma(x, fma(x, fma(x, c4, c3), c2), c1);
+}
+NB_HD __forceinline__ bool delta_phi_series(const TPow& r, double T9, double T9r, DPhi& d) {
+  const double dT = T9 - T9r;
+  const double x = dT * r.iT;
+  if ((dbits(x) & 0x7fffffffffffffffLL) > 0x3f10000000000000LL) return false;
+  d.d1 = r.iT * binom4(x, -1.0, 1.0, -1.0, 1.0);
+  d.d2 = r.it13 * binom4(x, -1.0 / 3.0, 2.0 / 9.0, -14.0 / 81.0, 35.0 / 243.0);
+  d.d3 = r.t13 * binom4(x, 1.0 / 3.0, -1.0 / 9.0, 5.0 / 81.0, -10.0 / 243.0);
+  d.d4 = dT;
+  d.d5 = r.T53 * binom4(x, 5.0 / 3.0, 5.0 / 9.0, -5.0 / 81.0, 5.0 / 243.0);
+  d.d6 = binom4(x, 1.0, -0.5, 1.0 / 3.0, -0.25);
+  d.d7 = r.hz * binom4(x, -1.5, 15.0 / 8.0, -35.0 / 16.0, 315.0 / 128.0);
+  return true;
+}
+
 NB_HD __forceinline__ double rate_delta(double a1, double a2, double a3, double a4,
                                         double a5, double a6, const DPhi& d) {
   double e1 = a1 * d.d1;
@@ -404,8 +461,8 @@ struct TRow {
 
 NB_HD __forceinline__ TRow t_row(double ed, double cv, double T9) {
   TRow r;
-  const double icv = 1.0 / cv;
-  const double fT = ed / cv;
+  const double icv = recip2(cv);
+  const double fT = ed * icv;
   r.a1 = icv;
   r.b1 = -fT * 1.5 * icv;
   r.b2 = -fT * (3e-3 * T9 * T9) * icv;
@@ -643,7 +700,7 @@ NB_HD __forceinline__ bool zone_init(const NT& t, Zone& s, WT& w, const BurnPara
   double s0 = 0.0, s1 = 0.0;
   NB_UNROLL
   for (int i = vbeg(t); i < n; i += vstep(t)) {
-    const double iw = 1.0 / (P.atol + P.rtol * fabs(x0[i]));
+    const double iw = recip1(P.atol + P.rtol * fabs(x0[i]));
     w.iw[i] = iw;
     const double a = x0[i] * iw, b = w.f0[i] * iw;
     s0 = fma(a, a, s0);
@@ -714,7 +771,7 @@ NB_HD __forceinline__ bool attempt_solve(const NT& t, Zone& s, WT& w, double ato
     const int b0 = hslot(s, 0) * n;
     NB_UNROLL
     for (int i = vbeg(t); i < n; i += vstep(t))
-      w.iw[i] = 1.0 / (atol + rtol * fabs(w.xh[b0 + i]));
+      w.iw[i] = recip1(atol + rtol * fabs(w.xh[b0 + i]));
   }
   // predictor
   if (s.nh >= kk + 1) extrapolate(t, s, w, 0, kk, t_new, w.xp);

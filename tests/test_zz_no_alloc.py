@@ -39,7 +39,7 @@ def _noalloc(torch, abi, lib, nc, Z, Y0, T9, rho, s, t_end_zone=None, zeta=None,
     Y = torch.full_like(Y0, np.nan)
     T = torch.full_like(T9, np.nan)
     E = torch.full_like(T9, np.nan)
-    cnt = torch.full((Z, nb.NCOUNT), -1, dtype=torch.int32, device=dev)
+    cnt = torch.full((Z, abi.NCOUNT), -1, dtype=torch.int32, device=dev)
     st = torch.full((Z,), -1, dtype=torch.int32, device=dev)
     stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
     rc = lib.nb_burn_batch_noalloc(
