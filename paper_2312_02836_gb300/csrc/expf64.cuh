@@ -25,7 +25,8 @@
 
 namespace nb {
 
-// S_j = 2^(j/32) = lead + trail, j = 0..31 (mpmath, 200-bit)
+// S_j = 2^(j/32) = lead + trail, j = 0..31 (mpmath, 200-bit; printed by
+// exp2_table.py beside this header)
 #define NB_EXP2_TABLE                                                     \
   0x1.0000000000000p+0, 0x0.0p+0, 0x1.059b0d3158574p+0, 0x1.d73e2a475b465p-55, \
   0x1.0b5586cf9890fp+0, 0x1.8a62e4adc610bp-54, 0x1.11301d0125b51p+0, -0x1.6c51039449b3ap-54, \

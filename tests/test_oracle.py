@@ -667,3 +667,25 @@ def test_per_zone_end_times_equal_separate_burns():
     c = oracle.burn(net, z["Y"], z["T9"], z["rho"], bad, s["rtol"], s["atol"])
     assert list(c["status"][1:3]) == [5, 5]
     assert np.array_equal(c["Y"][1:3], z["Y"][1:3])
+
+
+def test_exp_table_of_the_device_code_is_two_to_the_j_over_32():
+    # the double-double table of the device exp (Tang's method) against
+    # 2^(j/32) from mpmath, regenerated by the script beside the header
+    import re
+    import importlib.util
+    import os
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    csrc = os.path.join(root, "paper_2312_02836_gb300", "csrc")
+    spec = importlib.util.spec_from_file_location("exp2_table", os.path.join(csrc, "exp2_table.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    text = open(os.path.join(csrc, "expf64.cuh")).read()
+    body = text.split("#define NB_EXP2_TABLE", 1)[1].split("\n\n", 1)[0]
+    vals = [float.fromhex(v) for v in re.findall(r"-?0x[0-9a-f.]+p[+-]\d+", body)]
+    assert len(vals) == 64
+    assert vals == [v for lt in mod.table() for v in lt]
+    mpmath.mp.prec = 200
+    for j in range(32):
+        err = abs(mpmath.mpf(vals[2 * j]) + mpmath.mpf(vals[2 * j + 1]) - mpmath.mpf(2) ** (mpmath.mpf(j) / 32))
+        assert err < mpmath.mpf(2) ** -104
