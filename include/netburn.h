@@ -163,7 +163,11 @@ typedef struct {
   int32_t kernel;           /* NB_KERNEL_* */
   int32_t threads_per_block;/* 0 = 128; a multiple of 32, at most 256
                                (128 for the plain kernel) */
-  int32_t blocks_per_sm;    /* 0 = library choice (persistent kernel) */
+  int32_t blocks_per_sm;    /* 0 = library choice (persistent kernel); the
+                               warp kernel (NB_KERNEL_COOP) with >= 3 and
+                               threads_per_block <= 128 runs its variant
+                               built for three blocks per SM (registers
+                               capped at 168) */
   int32_t blob_in_shared;   /* -1 auto, 0 global (L1), 1 shared memory */
   int32_t ws_in_shared;     /* persistent kernel: the first ws_in_shared warps
                                of each block keep their Newton-loop arrays in

@@ -51,6 +51,9 @@ COOP_CANDIDATES = (
     # one block of four warps per SM: less shared memory taken, more L1 left
     # for the network's index lists
     dict(kernel="coop", threads_per_block=128, blocks_per_sm=1),
+    # three blocks of four warps per SM (registers capped, some spilled),
+    # where their shared-memory arrays fit
+    dict(kernel="coop", threads_per_block=128, blocks_per_sm=3),
 )
 
 DEFAULT_CANDIDATES = GENERIC_CANDIDATES + SPECIALIZED_CANDIDATES + COOP_CANDIDATES

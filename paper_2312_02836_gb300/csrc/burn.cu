@@ -74,7 +74,12 @@ __global__ void __launch_bounds__(256, 1) k_burn_persistent(BurnParams P) {
 // part of its arrays in shared memory after the (optional) blob copy and
 // only the history in the global workspace; otherwise everything is in the
 // global workspace, lane_doubles per warp.
-__global__ void __launch_bounds__(256, 1) k_burn_coop(BurnParams P) {
+// MINB 1: up to 8 warps a block, registers as the code wants (about 250);
+// MINB 3: blocks of up to 4 warps, three per SM, registers capped at 168
+// (some spilled to L1), for networks whose shared-memory arrays let three
+// blocks share an SM.
+template <int MINB>
+__global__ void __launch_bounds__(MINB == 1 ? 256 : 128, MINB) k_burn_coop(BurnParams P) {
   extern __shared__ __align__(16) unsigned char sm[];
   const unsigned char* blob = P.blob;
   if (P.blob_in_smem) {
@@ -404,6 +409,9 @@ static int launch_coop(nb_net net, BurnParams& P, const nb_options& o, cudaStrea
     in_smem = blob_b <= 96 * 1024 && blob_b + (hot_smem ? hot_warp : 0) <= net->smem_optin;
   const size_t fixed = in_smem ? blob_b : 0;
   int wpb;
+  // three blocks of at most four warps per SM when asked for
+  const bool dense = o.blocks_per_sm >= 3 && o.threads_per_block > 0 && o.threads_per_block <= 128;
+  const void* kern = dense ? (const void*)k_burn_coop<3> : (const void*)k_burn_coop<1>;
   if (o.threads_per_block > 0) {
     if (o.threads_per_block % 32 != 0 || o.threads_per_block > 256) return NB_E_ARG;
     wpb = o.threads_per_block / 32;
@@ -414,9 +422,9 @@ static int launch_coop(nb_net net, BurnParams& P, const nb_options& o, cudaStrea
   }
   const size_t dyn = fixed + (hot_smem ? (size_t)wpb * hot_warp : 0);
   if (dyn > net->smem_optin) return NB_E_TOO_LARGE;
-  CK(cudaFuncSetAttribute(k_burn_coop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+  CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
   int occ = 0;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_burn_coop, wpb * 32, dyn));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, wpb * 32, dyn));
   if (occ < 1) return NB_E_TOO_LARGE;
   const int bps = std::max(1, std::min(o.blocks_per_sm > 0 ? o.blocks_per_sm : occ, occ));
   long long blocks = (long long)bps * net->sm_count;
@@ -438,7 +446,10 @@ static int launch_coop(nb_net net, BurnParams& P, const nb_options& o, cudaStrea
     if (rc) return rc;
   }
   CK(cudaMemsetAsync(net->queue, 0, sizeof(unsigned long long), st));
-  k_burn_coop<<<(unsigned)blocks, wpb * 32, dyn, st>>>(P);
+  if (dense)
+    k_burn_coop<3><<<(unsigned)blocks, wpb * 32, dyn, st>>>(P);
+  else
+    k_burn_coop<1><<<(unsigned)blocks, wpb * 32, dyn, st>>>(P);
   CK(cudaGetLastError());
   return NB_OK;
 }

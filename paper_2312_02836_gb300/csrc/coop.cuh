@@ -91,8 +91,11 @@ __device__ __forceinline__ CWS make_cws(const Net& t, double* hot, double* cold)
   CWS w;
   w.x.p = hot + t.w_x; w.xp.p = hot + t.w_xp; w.psi.p = hot + t.w_psi;
   w.d.p = hot + t.w_d; w.f.p = hot + t.w_f; w.iw.p = hot + t.w_iw;
-  w.k.p = hot + t.w_k; w.g.p = hot + t.w_g; w.rr.p = hot + t.w_rr;
-  w.kp.p = hot + t.w_kp; w.dt.p = hot + t.w_dt; w.lu.p = hot + t.w_lu;
+  w.k.p = hot + t.w_k; w.rr.p = hot + t.w_rr;
+  w.dt.p = hot + t.w_dt; w.lu.p = hot + t.w_lu;
+  // g and kp sit with the cold part at fixed temperature
+  w.g.p = t.w_g < t.hot_doubles ? hot + t.w_g : cold + (t.w_g - t.hot_doubles);
+  w.kp.p = t.w_kp < t.hot_doubles ? hot + t.w_kp : cold + (t.w_kp - t.hot_doubles);
   w.tmp.p = cold + (t.w_tmp - t.hot_doubles);
   w.f0.p = cold + (t.w_f0 - t.hot_doubles);
   w.xh.p = cold + (t.w_xh - t.hot_doubles);

@@ -108,9 +108,12 @@ NB_HD __forceinline__ WS make_ws_split(const Net& t, double* hot_base, double* c
   w.f.p = hot_base + t.w_f * WS_LANES;
   w.iw.p = hot_base + t.w_iw * WS_LANES;
   w.k.p = hot_base + t.w_k * WS_LANES;
-  w.g.p = hot_base + t.w_g * WS_LANES;
+  // g and kp sit with the cold part at fixed temperature
+  w.g.p = t.w_g < t.hot_doubles ? hot_base + t.w_g * WS_LANES
+                                : cold_base + (t.w_g - t.hot_doubles) * WS_LANES;
   w.rr.p = hot_base + t.w_rr * WS_LANES;
-  w.kp.p = hot_base + t.w_kp * WS_LANES;
+  w.kp.p = t.w_kp < t.hot_doubles ? hot_base + t.w_kp * WS_LANES
+                                  : cold_base + (t.w_kp - t.hot_doubles) * WS_LANES;
   w.dt.p = hot_base + t.w_dt * WS_LANES;
   w.lu.p = hot_base + t.w_lu * WS_LANES;
   w.tmp.p = cold_base + (t.w_tmp - t.hot_doubles) * WS_LANES;

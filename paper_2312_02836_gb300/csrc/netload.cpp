@@ -445,10 +445,17 @@ int build_blob(const nb_topology* T, const double* coeffs,
   // placed in shared memory), then the history and start-up arrays
   h.w_x = take(n); h.w_xp = take(n); h.w_psi = take(n); h.w_d = take(n);
   h.w_f = take(n); h.w_iw = take(n);
-  h.w_k = take(R); h.w_g = take(R); h.w_rr = take(R); h.w_kp = take(R);
-  h.w_dt = take(nd + R);   // [dterms | R_r g_r]
+  // the T9 slopes g_r, the reference rates kp_r and the terms R_r g_r are
+  // Newton-loop arrays only with self-heating; at fixed temperature g_r is
+  // the adjoint's (the T9 gradient of the rates) and sits with the cold part
+  h.w_k = take(R);
+  if (sh) h.w_g = take(R);
+  h.w_rr = take(R);
+  if (sh) h.w_kp = take(R);
+  h.w_dt = take(nd + (sh ? R : 0));   // [dterms | R_r g_r]
   h.w_lu = take(nnz);
   h.hot_doubles = w;
+  if (!sh) { h.w_g = take(R); h.w_kp = take(R); }
   h.w_tmp = take(n); h.w_f0 = take(n);
   h.w_xh = take(HMAX * n); h.w_eh = take(HMAX); h.w_th = take(HMAX);
   h.lane_doubles = w;
