@@ -46,7 +46,8 @@ def test_newton_raphson_reciprocals(tmp_path):
         rng.uniform(1.0, 2.0, 200000) * 2.0 ** rng.integers(-1000, 1000, 200000),
         -rng.uniform(1.0, 2.0, 50000) * 2.0 ** rng.integers(-60, 60, 50000),
         np.array([1.0, -1.0, 3.0, 2.0 ** -1021, 2.0 ** 1020, 1.5 * 2.0 ** 1021,
-                  np.finfo(float).tiny, 5e-324, 0.0, -0.0, np.inf, np.nan]),
+                  1.5 * 2.0 ** 1022, np.finfo(float).tiny, 5e-324, 0.0, -0.0, np.inf,
+                  np.nan]),
     ])
     n = a.size
     r1, r2, rd = np.empty(n), np.empty(n), np.empty(n)
@@ -63,6 +64,6 @@ def test_newton_raphson_reciprocals(tmp_path):
     assert e2.max() <= 2.0
     assert e1.max() <= 2.0 ** -38
     # outside the normal range both take the division
-    odd = ~fin | (np.abs(a) < 2.0 ** -1022) | (np.abs(a) >= 2.0 ** 1021)
+    odd = ~fin | (np.abs(a) < 2.0 ** -1022) | (np.abs(a) >= 2.0 ** 1022)
     np.testing.assert_array_equal(r1[odd], exact[odd])
     np.testing.assert_array_equal(r2[odd], exact[odd])
