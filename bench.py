@@ -276,6 +276,8 @@ def run_native(args):
                       specialize=0 if args.specialize is None else args.specialize)
         if args.kernel != "persistent":
             launch["kernel"] = args.kernel
+            if args.warps_per_zone:
+                launch["warps_per_zone"] = args.warps_per_zone
         tune_ms = None
     else:
         from paper_2312_02836_gb300.autotune import autotune
@@ -673,6 +675,8 @@ def main():
     p.add_argument("--kernel", default="persistent", choices=["persistent", "coop"],
                    help="the main workload's kernel (coop: one warp per zone); "
                         "persistent lets the autotuner choose")
+    p.add_argument("--warps-per-zone", type=int, default=0,
+                   help="with --kernel coop: a block of 2 or 4 warps per zone")
     p.add_argument("--cpu-zones", type=int, default=8192)
     p.add_argument("--ref-zones", type=int, default=4096)
     p.add_argument("--no-cpu-baseline", action="store_true")

@@ -207,6 +207,14 @@ typedef struct {
                                for screening, or NULL (no screening).  A
                                negative or non-finite entry gives that zone
                                NB_Z_NONFINITE. */
+  int32_t warps_per_zone;   /* NB_KERNEL_COOP: 0 or 1, one warp per zone;
+                               2 or 4, a block of that many warps integrates
+                               one zone (one zone per block, its arrays in
+                               shared memory once, the LU pairs, reactions
+                               and slots spread over 64 or 128 threads):
+                               for networks whose per-zone arrays let few
+                               warps share an SM.  threads_per_block is then
+                               ignored.  Other values: NB_E_ARG. */
 } nb_options;
 
 #define NB_KERNEL_AUTO (-1)     /* adjoint only: the choice made for opt NULL */

@@ -155,7 +155,7 @@ class BurnResult(NamedTuple):
 
 def _options(kernel, threads_per_block, blocks_per_sm, blob_in_shared,
              max_attempts, ws_in_shared=-1, time_budget_s=0.0, schedule=None,
-             specialize=0):
+             specialize=0, warps_per_zone=0):
     o = _abi.Options()
     _abi.load().nb_default_options(C.byref(o))
     if isinstance(kernel, str):
@@ -171,6 +171,7 @@ def _options(kernel, threads_per_block, blocks_per_sm, blob_in_shared,
     if schedule is not None:
         o.schedule = {"fifo": 0, "longest_first": 1}.get(schedule, schedule)
     o.specialize = {"auto": 0, "generic": -1, None: 0}.get(specialize, specialize)
+    o.warps_per_zone = int(warps_per_zone)
     return o
 
 
@@ -190,14 +191,16 @@ def burn(net: Network, Y0, T9, rho, t_end: float, rtol: float, atol: float,
          ln_mult=None, *, kernel="persistent", tape: "Optional[Tape]" = None,
          threads_per_block=0, blocks_per_sm=0, blob_in_shared=-1,
          ws_in_shared=-1, max_attempts=500000, time_budget_s=0.0, schedule=None,
-         specialize=0, zeta=None, stream=None, out: Optional[BurnResult] = None):
+         specialize=0, zeta=None, warps_per_zone=0, stream=None,
+         out: Optional[BurnResult] = None):
     """Burn Z zones on the GPU.  Y0 [Z,N], T9 [Z], rho [Z] CUDA float64;
     t_end a number, or a CUDA float64 tensor [Z] of per-zone end times;
     ln_mult None, [R] or [Z,R].  specialize: 0/"auto" the kernel generated
     for the network when it qualifies, -1/"generic" the generic kernel, 1..3
     a specialised storage variant.  zeta: None or a CUDA float64 tensor [Z]
     of per-zone plasma parameters (weak screening of a screened network).
-    Returns BurnResult of CUDA tensors."""
+    warps_per_zone (kernel "coop"): 1, or 2 or 4 warps of one block per
+    zone.  Returns BurnResult of CUDA tensors."""
     torch = _torch()
     Z = int(Y0.shape[0]) if Y0.dim() == 2 else 0
     _dev(Y0, torch, "Y0", (Z, net.N))
@@ -220,7 +223,8 @@ def burn(net: Network, Y0, T9, rho, t_end: float, rtol: float, atol: float,
                          torch.empty((Z, NCOUNT), dtype=torch.int32, device=dev),
                          torch.empty((Z,), dtype=torch.int32, device=dev))
     o = _options(kernel, threads_per_block, blocks_per_sm, blob_in_shared,
-                 max_attempts, ws_in_shared, time_budget_s, schedule, specialize)
+                 max_attempts, ws_in_shared, time_budget_s, schedule, specialize,
+                 warps_per_zone)
     if isinstance(t_end, torch.Tensor):
         # operator split: every zone burns for its own step
         _dev(t_end, torch, "t_end", (Z,))

@@ -75,7 +75,7 @@ class Options(C.Structure):
                 ("blob_in_shared", C.c_int32), ("ws_in_shared", C.c_int32),
                 ("schedule", C.c_int32), ("specialize", C.c_int32),
                 ("t_end_zone", C.c_void_p), ("time_budget_s", C.c_double),
-                ("zeta_zone", C.c_void_p)]
+                ("zeta_zone", C.c_void_p), ("warps_per_zone", C.c_int32)]
 
 
 def load(build_if_needed: bool = True):

@@ -54,6 +54,10 @@ COOP_CANDIDATES = (
     # three blocks of four warps per SM (registers capped, some spilled),
     # where their shared-memory arrays fit
     dict(kernel="coop", threads_per_block=128, blocks_per_sm=3),
+    # a block of two or four warps per zone: more lanes on each zone's LU
+    # where the arrays of one zone take much of an SM's shared memory
+    dict(kernel="coop", warps_per_zone=2),
+    dict(kernel="coop", warps_per_zone=4),
 )
 
 DEFAULT_CANDIDATES = GENERIC_CANDIDATES + SPECIALIZED_CANDIDATES + COOP_CANDIDATES

@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(256, 1) k_adjoint_coop(AdjParams A, CoopAdj C)
     __syncthreads();
     blob = sm;
   }
-  const WNet t = make_wnet(blob, threadIdx.x & 31);
+  const WNet t = make_wnet<32>(blob, threadIdx.x & 31);
   const int wib = threadIdx.x >> 5;
   const long long warp = (long long)blockIdx.x * (blockDim.x >> 5) + wib;
   const long long fwd = t.g.lane_doubles;

@@ -70,16 +70,20 @@ __global__ void __launch_bounds__(256, 1) k_burn_persistent(BurnParams P) {
   burn_claim_loop(t, w, P);
 }
 
-// One warp per zone.  With P.smem_warps > 0 every warp keeps the Newton-loop
-// part of its arrays in shared memory after the (optional) blob copy and
-// only the history in the global workspace; otherwise everything is in the
-// global workspace, lane_doubles per warp.
-// MINB 1: up to 8 warps a block, registers as the code wants (about 250);
+// One zone per team of W threads: a warp (W = 32, every warp of the block
+// its own team), or the whole block (W = 64 or 128).  With P.smem_warps > 0
+// every team keeps the Newton-loop part of its arrays in shared memory after
+// the (optional) blob copy and only the history in the global workspace;
+// otherwise everything is in the global workspace, lane_doubles per team.
+// A team larger than a warp has its sums' partials and its broadcast slot
+// after its arrays in shared memory.
+// MINB 1: blocks of up to 8 warps, registers as the code wants (about 250);
 // MINB 3: blocks of up to 4 warps, three per SM, registers capped at 168
 // (some spilled to L1), for networks whose shared-memory arrays let three
 // blocks share an SM.
-template <int MINB>
-__global__ void __launch_bounds__(MINB == 1 ? 256 : 128, MINB) k_burn_coop(BurnParams P) {
+template <int MINB, int W>
+__global__ void __launch_bounds__(W > 32 ? W : (MINB == 1 ? 256 : 128), MINB)
+    k_burn_coop(BurnParams P) {
   extern __shared__ __align__(16) unsigned char sm[];
   const unsigned char* blob = P.blob;
   if (P.blob_in_smem) {
@@ -89,16 +93,19 @@ __global__ void __launch_bounds__(MINB == 1 ? 256 : 128, MINB) k_burn_coop(BurnP
     __syncthreads();
     blob = sm;
   }
-  const WNet t = make_wnet(blob, threadIdx.x & 31);
-  const int wib = threadIdx.x >> 5;
-  const long long warp = (long long)blockIdx.x * (blockDim.x >> 5) + wib;
+  double* smd = reinterpret_cast<double*>(sm + (P.blob_in_smem ? P.blob_bytes : 0));
+  const int tib = threadIdx.x / W;
+  const long long team = (long long)blockIdx.x * (blockDim.x / W) + tib;
+  const BlobHeader* bh = reinterpret_cast<const BlobHeader*>(blob);
+  double* red = nullptr;
+  if constexpr (W > 32) red = smd + (P.smem_warps > 0 ? bh->hot_doubles : 0);
+  const WNetT<W> t = make_wnet<W>(blob, threadIdx.x % W, red);
   double *hot, *cold;
   if (P.smem_warps > 0) {
-    hot = reinterpret_cast<double*>(sm + (P.blob_in_smem ? P.blob_bytes : 0)) +
-          (size_t)wib * t.g.hot_doubles;
-    cold = P.ws + warp * (long long)(t.g.lane_doubles - t.g.hot_doubles);
+    hot = smd + (size_t)tib * t.g.hot_doubles;
+    cold = P.ws + team * (long long)(t.g.lane_doubles - t.g.hot_doubles);
   } else {
-    hot = P.ws + warp * (long long)t.g.lane_doubles;
+    hot = P.ws + team * (long long)t.g.lane_doubles;
     cold = hot + t.g.hot_doubles;
   }
   CWS w = make_cws(t.g, hot, cold);
@@ -401,55 +408,70 @@ static int schedule_longest_first(nb_net net, BurnParams& P, long long lanes,
 // fit; blob_in_shared as for the persistent kernel.
 static int launch_coop(nb_net net, BurnParams& P, const nb_options& o, cudaStream_t st) {
   const size_t blob_b = (size_t)net->h.bytes;
-  const size_t hot_warp = (size_t)net->h.hot_doubles * sizeof(double);
-  const size_t warp_doubles = (size_t)net->h.lane_doubles;
-  const bool hot_smem = o.ws_in_shared != 0 && hot_warp <= net->smem_optin;
+  const size_t hot_team = (size_t)net->h.hot_doubles * sizeof(double);
+  const size_t team_doubles = (size_t)net->h.lane_doubles;
+  const int wpz = o.warps_per_zone <= 1 ? 1 : o.warps_per_zone;
+  if (o.warps_per_zone < 0 || (wpz != 1 && wpz != 2 && wpz != 4)) return NB_E_ARG;
+  const size_t scratch = (size_t)team_scratch_doubles(32 * wpz) * sizeof(double);
+  const bool hot_smem = o.ws_in_shared != 0 && hot_team + scratch <= net->smem_optin;
   int in_smem = o.blob_in_shared;
   if (in_smem < 0)
-    in_smem = blob_b <= 96 * 1024 && blob_b + (hot_smem ? hot_warp : 0) <= net->smem_optin;
-  const size_t fixed = in_smem ? blob_b : 0;
-  int wpb;
-  // three blocks of at most four warps per SM when asked for
-  const bool dense = o.blocks_per_sm >= 3 && o.threads_per_block > 0 && o.threads_per_block <= 128;
-  const void* kern = dense ? (const void*)k_burn_coop<3> : (const void*)k_burn_coop<1>;
-  if (o.threads_per_block > 0) {
+    in_smem = blob_b <= 96 * 1024 &&
+              blob_b + (hot_smem ? hot_team : 0) + scratch <= net->smem_optin;
+  const size_t fixed = (in_smem ? blob_b : 0) + scratch;
+  // teams per block; three blocks of at most four warps per SM when asked for
+  int tpb_teams;
+  const bool dense =
+      wpz == 1 && o.blocks_per_sm >= 3 && o.threads_per_block > 0 && o.threads_per_block <= 128;
+  const void* kern = wpz == 4 ? (const void*)k_burn_coop<1, 128>
+                   : wpz == 2 ? (const void*)k_burn_coop<1, 64>
+                   : dense    ? (const void*)k_burn_coop<3, 32>
+                              : (const void*)k_burn_coop<1, 32>;
+  if (wpz > 1) {
+    tpb_teams = 1;
+  } else if (o.threads_per_block > 0) {
     if (o.threads_per_block % 32 != 0 || o.threads_per_block > 256) return NB_E_ARG;
-    wpb = o.threads_per_block / 32;
+    tpb_teams = o.threads_per_block / 32;
   } else {
-    wpb = 4;
+    tpb_teams = 4;
     if (hot_smem)
-      while (wpb > 1 && fixed + (size_t)wpb * hot_warp > net->smem_optin) --wpb;
+      while (tpb_teams > 1 && fixed + (size_t)tpb_teams * hot_team > net->smem_optin) --tpb_teams;
   }
-  const size_t dyn = fixed + (hot_smem ? (size_t)wpb * hot_warp : 0);
+  const int threads = wpz > 1 ? 32 * wpz : 32 * tpb_teams;
+  const size_t dyn = fixed + (hot_smem ? (size_t)tpb_teams * hot_team : 0);
   if (dyn > net->smem_optin) return NB_E_TOO_LARGE;
   CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
   int occ = 0;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, wpb * 32, dyn));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, dyn));
   if (occ < 1) return NB_E_TOO_LARGE;
   const int bps = std::max(1, std::min(o.blocks_per_sm > 0 ? o.blocks_per_sm : occ, occ));
   long long blocks = (long long)bps * net->sm_count;
-  const long long needed = (P.Z + wpb - 1) / wpb;
+  const long long needed = (P.Z + tpb_teams - 1) / tpb_teams;
   if (blocks > needed) blocks = needed;
-  const size_t per_warp = (hot_smem ? warp_doubles - net->h.hot_doubles : warp_doubles) * 8;
-  size_t need = std::max<size_t>((size_t)blocks * wpb * per_warp, 256);
-  const size_t lane_bytes = warp_doubles * sizeof(double);
+  const size_t per_team = (hot_smem ? team_doubles - net->h.hot_doubles : team_doubles) * 8;
+  size_t need = std::max<size_t>((size_t)blocks * tpb_teams * per_team, 256);
+  const size_t lane_bytes = team_doubles * sizeof(double);
   if (o.schedule == 1) need = std::max(need, (size_t)128 * lane_bytes);  // pre-pass lanes
   int rc = nb::ensure((void**)&net->ws, &net->ws_bytes, need);
   if (rc) return rc;
   P.ws = net->ws;
   P.queue = net->queue;
   P.blob_in_smem = in_smem;
-  P.smem_warps = hot_smem ? wpb : 0;
+  P.smem_warps = hot_smem ? tpb_teams : 0;
   P.order = nullptr;
   if (o.schedule == 1 && P.Z > 1) {
     rc = schedule_longest_first(net, P, 128, st);
     if (rc) return rc;
   }
   CK(cudaMemsetAsync(net->queue, 0, sizeof(unsigned long long), st));
-  if (dense)
-    k_burn_coop<3><<<(unsigned)blocks, wpb * 32, dyn, st>>>(P);
+  if (wpz == 4)
+    k_burn_coop<1, 128><<<(unsigned)blocks, threads, dyn, st>>>(P);
+  else if (wpz == 2)
+    k_burn_coop<1, 64><<<(unsigned)blocks, threads, dyn, st>>>(P);
+  else if (dense)
+    k_burn_coop<3, 32><<<(unsigned)blocks, threads, dyn, st>>>(P);
   else
-    k_burn_coop<1><<<(unsigned)blocks, wpb * 32, dyn, st>>>(P);
+    k_burn_coop<1, 32><<<(unsigned)blocks, threads, dyn, st>>>(P);
   CK(cudaGetLastError());
   return NB_OK;
 }

@@ -30,36 +30,81 @@ namespace nb {
 
 constexpr unsigned kFullMask = 0xffffffffu;
 
-// The compiled network seen by one lane of the warp that owns a zone.
-struct WNet {
+// The compiled network seen by one of the W threads that own a zone: a warp
+// (W = 32), or a block of two or four warps (W = 64, 128) for networks whose
+// per-pivot work fills more lanes than a warp has.  A team larger than a
+// warp is one whole block, so its barrier is the block's.
+template <int W>
+struct WNetT {
+  static constexpr int width = W;
   Net g;
   int n, N, R, sh, hasE;
   double inv_n;
-  int lane;
+  int lane;   // 0 .. W-1
   const int16_t *perm, *ltgt, *ucol_s, *ucol_t, *utgt, *lrow_s, *lrow_t, *dej_d;
   const int32_t *ucol_ptr, *lrow_ptr, *dej_ptr;
-  // sum over the warp, the same bits in every lane (an xor butterfly adds
-  // the same two operands in both lanes of each pair)
+  // W > 32: two alternating rows of W/32 partial sums and a broadcast slot
+  // in shared memory
+  double* red;
+  mutable int ph;
+  // sum over the team, the same bits in every thread: an xor butterfly in
+  // each warp (it adds the same two operands in both lanes of each pair),
+  // then the warps' sums added in warp order
   __device__ __forceinline__ double sum(double x) const {
 #pragma unroll
     for (int m = 16; m >= 1; m >>= 1) x += __shfl_xor_sync(kFullMask, x, m);
+    if constexpr (W > 32) {
+      double* row = red + ph * (W / 32);
+      ph ^= 1;
+      if ((lane & 31) == 0) row[lane >> 5] = x;
+      __syncthreads();
+      x = row[0];
+#pragma unroll
+      for (int q = 1; q < W / 32; ++q) x += row[q];
+    }
     return x;
   }
-  __device__ __forceinline__ bool all(bool b) const { return __all_sync(kFullMask, b); }
-  __device__ __forceinline__ void sync() const { __syncwarp(); }
+  __device__ __forceinline__ bool all(bool b) const {
+    if constexpr (W > 32) return __syncthreads_and(b) != 0;
+    else return __all_sync(kFullMask, b);
+  }
+  __device__ __forceinline__ void sync() const {
+    if constexpr (W > 32) __syncthreads();
+    else __syncwarp();
+  }
+  // thread 0's value in every thread of the team
+  __device__ __forceinline__ unsigned long long bcast(unsigned long long v) const {
+    if constexpr (W > 32) {
+      unsigned long long* slot = reinterpret_cast<unsigned long long*>(red + 2 * (W / 32));
+      __syncthreads();
+      if (lane == 0) *slot = v;
+      __syncthreads();
+      return *slot;
+    } else {
+      return __shfl_sync(kFullMask, v, 0);
+    }
+  }
 };
+using WNet = WNetT<32>;
 
-template <>
-struct is_coop<WNet> {
+// shared-memory doubles a team of W threads needs for its sums and broadcasts
+constexpr int team_scratch_doubles(int W) { return W > 32 ? 2 * (W / 32) + 1 : 0; }
+
+template <int W>
+struct is_coop<WNetT<W>> {
   static constexpr bool value = true;
 };
 
-__device__ __forceinline__ WNet make_wnet(const unsigned char* blob, int lane) {
-  WNet t;
+template <int W>
+__device__ __forceinline__ WNetT<W> make_wnet(const unsigned char* blob, int lane,
+                                              double* red = nullptr) {
+  WNetT<W> t;
   t.g = make_net(blob);
   t.n = t.g.n; t.N = t.g.N; t.R = t.g.R; t.sh = t.g.sh; t.hasE = t.g.hasE;
   t.inv_n = t.g.inv_n;
   t.lane = lane;
+  t.red = red;
+  t.ph = 0;
   const BlobHeader* h = reinterpret_cast<const BlobHeader*>(blob);
   t.perm = at<int16_t>(blob, h->o_perm);
   t.ltgt = at<int16_t>(blob, h->o_ltgt);
@@ -106,27 +151,30 @@ __device__ __forceinline__ CWS make_cws(const Net& t, double* hot, double* cold)
 
 // ---------------------------------------------------------------- model
 
-__device__ __forceinline__ void eval_rates(const WNet& t, const Zone& s, const CWS& w,
+template <int W>
+__device__ __forceinline__ void eval_rates(const WNetT<W>& t, const Zone& s, const CWS& w,
                                            const TPow& p, double T9, bool with_g) {
-  __syncwarp();
+  t.sync();
   const Net& g = t.g;
   const TCell tc = g.tab_of ? t_cell(g.tab_t9, g.tab_nt, T9) : TCell{0, 0.0, 1.0, false};
-  for (int r = t.lane; r < t.R; r += 32) {
+  for (int r = t.lane; r < t.R; r += W) {
     double gr;
     w.k[r] = rate_full(g, s, r, p, T9, tc, with_g ? &gr : nullptr);
     if (with_g) w.g[r] = gr;
   }
-  __syncwarp();
+  t.sync();
 }
 
-__device__ __forceinline__ void save_ref_rates(const WNet& t, const CWS& w) {
-  for (int r = t.lane; r < t.R; r += 32) w.kp[r] = w.k[r];
-  __syncwarp();
+template <int W>
+__device__ __forceinline__ void save_ref_rates(const WNetT<W>& t, const CWS& w) {
+  for (int r = t.lane; r < t.R; r += W) w.kp[r] = w.k[r];
+  t.sync();
 }
 
-__device__ __forceinline__ void eval_rates_near(const WNet& t, const Zone& s, const CWS& w,
+template <int W>
+__device__ __forceinline__ void eval_rates_near(const WNetT<W>& t, const Zone& s, const CWS& w,
                                                 double T9, const TPow& ref, double T9ref) {
-  __syncwarp();
+  t.sync();
   const Net& g = t.g;
   DPhi d;
   TPow p;
@@ -136,7 +184,7 @@ __device__ __forceinline__ void eval_rates_near(const WNet& t, const Zone& s, co
     d = delta_phi(p, ref, T9, T9ref);
   }
   const TCell tc = g.tab_of ? t_cell(g.tab_t9, g.tab_nt, T9) : TCell{0, 0.0, 1.0, false};
-  for (int r = t.lane; r < t.R; r += 32) {
+  for (int r = t.lane; r < t.R; r += W) {
     const double* a = g.coef + 7 * r;
     double de = rate_delta(a[1], a[2], a[3], a[4], a[5], a[6], d);
     if (g.scr) de = fma(g.scr[r], d.d7, de);
@@ -150,20 +198,21 @@ __device__ __forceinline__ void eval_rates_near(const WNet& t, const Zone& s, co
       w.k[r] = rate_full(g, s, r, p, T9, tc, nullptr);
     }
   }
-  __syncwarp();
+  t.sync();
 }
 
 // the zone's density cell of the rate tables (every lane, the same sum)
-template <class V>
-__device__ __forceinline__ void tab_zone(const WNet& t, Zone& s, const V& x0) {
-  __syncwarp();
+template <int W, class V>
+__device__ __forceinline__ void tab_zone(const WNetT<W>& t, Zone& s, const V& x0) {
+  t.sync();
   tab_zone(t.g, s, x0);
 }
 
-__device__ __forceinline__ void eval_terms(const WNet& t, const CWS& w, const CV& v) {
-  __syncwarp();
+template <int W>
+__device__ __forceinline__ void eval_terms(const WNetT<W>& t, const CWS& w, const CV& v) {
+  t.sync();
   const Net& g = t.g;
-  for (int r = t.lane; r < t.R; r += 32) {
+  for (int r = t.lane; r < t.R; r += W) {
     const int16_t* ra = g.reac + 3 * r;
     const int m = g.nreac[r];
     double q = w.k[r];
@@ -172,13 +221,14 @@ __device__ __forceinline__ void eval_terms(const WNet& t, const CWS& w, const CV
     if (m > 2) q *= v[ra[2]];
     w.rr[r] = q;
   }
-  __syncwarp();
+  t.sync();
 }
 
 // sum_r Q_r rr_r, the same value in every lane
-__device__ __forceinline__ double eval_edot(const WNet& t, const CWS& w) {
+template <int W>
+__device__ __forceinline__ double eval_edot(const WNetT<W>& t, const CWS& w) {
   double e = 0.0;
-  for (int r = t.lane; r < t.R; r += 32) e = fma(t.g.Q[r], w.rr[r], e);
+  for (int r = t.lane; r < t.R; r += W) e = fma(t.g.Q[r], w.rr[r], e);
   return t.sum(e);
 }
 
@@ -196,24 +246,26 @@ __device__ __forceinline__ double gather(const double* c, const TI* idx, int beg
   return a0 + a1;
 }
 
-__device__ __forceinline__ void eval_f(const WNet& t, const CWS& w, const CV& v, const CV& out) {
-  __syncwarp();
+template <int W>
+__device__ __forceinline__ void eval_f(const WNetT<W>& t, const CWS& w, const CV& v, const CV& out) {
+  t.sync();
   const Net& g = t.g;
-  for (int i = t.lane; i < t.N; i += 32)
+  for (int i = t.lane; i < t.N; i += W)
     out[i] = gather(g.rhs_c, g.rhs_r, g.rhs_ptr[i], g.rhs_ptr[i + 1], w.rr);
   if (t.sh) {
     const double fT = eval_edot(t, w) / heat_capacity(t, v);
     if (t.lane == 0) out[t.N] = fT;
   }
-  __syncwarp();
+  t.sync();
 }
 
 // M = alpha0 I - h J(v) into w.lu (needs w.k, w.g (self-heating), w.rr at v)
-__device__ __forceinline__ void assemble_M(const WNet& t, const CWS& w, const CV& v,
+template <int W>
+__device__ __forceinline__ void assemble_M(const WNetT<W>& t, const CWS& w, const CV& v,
                                            double alpha0, double h) {
-  __syncwarp();
+  t.sync();
   const Net& g = t.g;
-  for (int d = t.lane; d < g.nd; d += 32) {
+  for (int d = t.lane; d < g.nd; d += W) {
     const int16_t o0 = g.dt_o[2 * d], o1 = g.dt_o[2 * d + 1];
     double q = w.k[g.dt_r[d]] * g.dt_m[d];
     if (o0 >= 0) q *= v[o0];
@@ -222,12 +274,12 @@ __device__ __forceinline__ void assemble_M(const WNet& t, const CWS& w, const CV
   }
   TRow tr{0.0, 0.0, 0.0};
   if (t.sh) {
-    for (int r = t.lane; r < t.R; r += 32) w.dt[g.nd + r] = w.rr[r] * w.g[r];
+    for (int r = t.lane; r < t.R; r += W) w.dt[g.nd + r] = w.rr[r] * w.g[r];
     tr = t_row(eval_edot(t, w), heat_capacity(t, v), v[t.N]);
   }
-  __syncwarp();
+  t.sync();
   const double mh = -h;
-  for (int s = t.lane; s < g.nnz; s += 32) {
+  for (int s = t.lane; s < g.nnz; s += W) {
     double acc = gather(g.js_c, g.js_src, g.js_ptr[s], g.js_ptr[s + 1], w.dt);
     const uint8_t fl = g.js_flag[s];
     if (fl & SLOT_TROW) acc = fma(acc, tr.a1, tr.b1);
@@ -236,17 +288,18 @@ __device__ __forceinline__ void assemble_M(const WNet& t, const CWS& w, const CV
     if (fl & SLOT_DIAG) m += alpha0;
     w.lu[s] = m;
   }
-  __syncwarp();
+  t.sync();
 }
 
 // Static-pivot LU in place, the diagonal keeping 1/pivot; the lane
 // kernel's operations slot by slot.  false if a pivot is zero, not finite
 // or eaten by cancellation (pivot_kept).
-__device__ __forceinline__ bool factor_M(const WNet& t, const CWS& w) {
-  __syncwarp();
+template <int W>
+__device__ __forceinline__ bool factor_M(const WNetT<W>& t, const CWS& w) {
+  t.sync();
   const Net& g = t.g;
-  for (int k = t.lane; k < t.n; k += 32) w.tmp[k] = w.lu[g.piv[k].dslot];
-  __syncwarp();
+  for (int k = t.lane; k < t.n; k += W) w.tmp[k] = w.lu[g.piv[k].dslot];
+  t.sync();
   bool ok = true;
   for (int k = 0; k < t.n; ++k) {
     const Pivot p = g.piv[k];
@@ -254,83 +307,84 @@ __device__ __forceinline__ bool factor_M(const WNet& t, const CWS& w) {
     ok = ok && pivot_kept(pv, w.tmp[k]);
     const double inv = recip2(pv);
     const int nl = p.lend - p.lbeg, nu = p.uend - p.ubeg;
-    for (int li = p.lbeg + t.lane; li < p.lend; li += 32) {
+    for (int li = p.lbeg + t.lane; li < p.lend; li += W) {
       const int ls = g.lslot[li];
       w.lu[ls] = w.lu[ls] * inv;
     }
-    __syncwarp();
+    t.sync();
     if (t.lane == 0) w.lu[p.dslot] = inv;
     const int np = nl * nu;
     if (np > 0) {
-      // pair e = li * nu + u, walked in steps of 32 without a division per pair
-      const int q32 = 32 / nu, r32 = 32 - q32 * nu;
+      // pair e = li * nu + u, walked in steps of W without a division per pair
+      const int qW = W / nu, rW = W - qW * nu;
       int li = t.lane / nu, u = t.lane - li * nu;
-      for (int e = t.lane; e < np; e += 32) {
+      for (int e = t.lane; e < np; e += W) {
         const int ds = g.dslot[p.dbeg + e];
         const double l = w.lu[g.lslot[p.lbeg + li]];
         w.lu[ds] = fma(-l, w.lu[g.uslot[p.ubeg + u]], w.lu[ds]);
-        li += q32;
-        u += r32;
+        li += qW;
+        u += rW;
         if (u >= nu) { u -= nu; ++li; }
       }
     }
-    __syncwarp();
+    t.sync();
   }
   return ok;
 }
 
 // v <- M^-1 v with the factored w.lu: L column by column, then U column by
 // column from the last
-__device__ __forceinline__ void solve_M(const WNet& t, const CWS& w, const CV& v) {
-  __syncwarp();
+template <int W>
+__device__ __forceinline__ void solve_M(const WNetT<W>& t, const CWS& w, const CV& v) {
+  t.sync();
   const Net& g = t.g;
   for (int k = 0; k < t.n; ++k) {
     const Pivot p = g.piv[k];
     const double vk = v[t.perm[k]];
-    for (int li = p.lbeg + t.lane; li < p.lend; li += 32) {
+    for (int li = p.lbeg + t.lane; li < p.lend; li += W) {
       const int r = t.ltgt[li];
       v[r] = fma(-w.lu[g.lslot[li]], vk, v[r]);
     }
-    __syncwarp();
+    t.sync();
   }
   for (int k = t.n - 1; k >= 0; --k) {
     const int pk = t.perm[k];
     const double xk = v[pk] * w.lu[g.piv[k].dslot];
-    __syncwarp();
+    t.sync();
     if (t.lane == 0) v[pk] = xk;
-    for (int e = t.ucol_ptr[k] + t.lane; e < t.ucol_ptr[k + 1]; e += 32) {
+    for (int e = t.ucol_ptr[k] + t.lane; e < t.ucol_ptr[k + 1]; e += W) {
       const int r = t.ucol_t[e];
       v[r] = fma(-w.lu[t.ucol_s[e]], xk, v[r]);
     }
-    __syncwarp();
+    t.sync();
   }
 }
 
 // v <- M^-T v with the factored w.lu (the adjoint): U^T column by column
 // (pivot rows of U), then L^T column by column from the last (rows of L)
-template <class V>
-__device__ __forceinline__ void solve_MT(const WNet& t, const CV& lu, const V& v) {
-  __syncwarp();
+template <int W, class V>
+__device__ __forceinline__ void solve_MT(const WNetT<W>& t, const CV& lu, const V& v) {
+  t.sync();
   const Net& g = t.g;
   for (int k = 0; k < t.n; ++k) {
     const Pivot p = g.piv[k];
     const int pk = t.perm[k];
     const double xk = v[pk] * lu[p.dslot];
-    __syncwarp();
+    t.sync();
     if (t.lane == 0) v[pk] = xk;
-    for (int u = p.ubeg + t.lane; u < p.uend; u += 32) {
+    for (int u = p.ubeg + t.lane; u < p.uend; u += W) {
       const int r = t.utgt[u];
       v[r] = fma(-lu[g.uslot[u]], xk, v[r]);
     }
-    __syncwarp();
+    t.sync();
   }
   for (int k = t.n - 1; k >= 0; --k) {
     const double xk = v[t.perm[k]];
-    for (int e = t.lrow_ptr[k] + t.lane; e < t.lrow_ptr[k + 1]; e += 32) {
+    for (int e = t.lrow_ptr[k] + t.lane; e < t.lrow_ptr[k + 1]; e += W) {
       const int r = t.lrow_t[e];
       v[r] = fma(-lu[t.lrow_s[e]], xk, v[r]);
     }
-    __syncwarp();
+    t.sync();
   }
 }
 
@@ -339,19 +393,19 @@ __device__ __forceinline__ void solve_MT(const WNet& t, const CV& lu, const V& v
 // One zone per warp: lane 0 claims zones from the device queue and every
 // lane of the warp integrates it.  The watchdog reads lane 0's clock, so the
 // warp decides as one.
-template <class WT>
-__device__ __forceinline__ void coop_claim_loop(const WNet& t, WT& w, const BurnParams& P) {
+template <int W, class WT>
+__device__ __forceinline__ void coop_claim_loop(const WNetT<W>& t, WT& w, const BurnParams& P) {
   unsigned long long t_start = 0ull;
-  if (P.budget_ns) t_start = __shfl_sync(kFullMask, t.lane == 0 ? gpu_ns() : 0ull, 0);
+  if (P.budget_ns) t_start = t.bcast(t.lane == 0 ? gpu_ns() : 0ull);
   auto expired = [&]() {
     if (!P.budget_ns) return false;
-    const unsigned long long now = __shfl_sync(kFullMask, t.lane == 0 ? gpu_ns() : 0ull, 0);
+    const unsigned long long now = t.bcast(t.lane == 0 ? gpu_ns() : 0ull);
     return now - t_start > P.budget_ns;
   };
   for (;;) {
     unsigned long long c = 0;
     if (t.lane == 0) c = atomicAdd(P.queue, 1ull);
-    c = __shfl_sync(kFullMask, c, 0);
+    c = t.bcast(c);
     if (c >= (unsigned long long)P.Z) break;
     Zone s;
     s.z = P.order ? (long long)P.order[c] : (long long)c;
@@ -368,7 +422,7 @@ __device__ __forceinline__ void coop_claim_loop(const WNet& t, WT& w, const Burn
       done = zone_attempt(t, s, w, P);
     }
     zone_finish(t, s, w, P);
-    __syncwarp();
+    t.sync();
   }
 }
 

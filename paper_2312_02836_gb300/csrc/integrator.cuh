@@ -67,7 +67,7 @@ NB_HD __forceinline__ constexpr int vbeg(const NT& t) {
 }
 template <class NT>
 NB_HD __forceinline__ constexpr int vstep(const NT&) {
-  if constexpr (is_coop<NT>::value) return 32; else return 1;
+  if constexpr (is_coop<NT>::value) return NT::width; else return 1;
 }
 // sum over the zone's threads of their partial sums (the same bits in all)
 template <class NT>

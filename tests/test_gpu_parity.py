@@ -63,12 +63,15 @@ CASES = [("chain13", 4096), ("chain13_literal", 1024), ("chain13_heat", 2048),
 # "persistent": the default persistent launch (the network-specialised kernel
 # where the network qualifies); "generic": the persistent launch forced onto
 # the generic kernel; "plain": one thread per zone; "coop": one warp per zone;
-# "coop3": one warp per zone in the variant built for three blocks per SM
+# "coop3": one warp per zone in the variant built for three blocks per SM;
+# "team2", "team4": a block of two or four warps per zone
 KERNELS = {"persistent": dict(kernel="persistent"),
            "generic": dict(kernel="persistent", specialize="generic"),
            "plain": dict(kernel="plain"),
            "coop": dict(kernel="coop"),
-           "coop3": dict(kernel="coop", threads_per_block=32, blocks_per_sm=3)}
+           "coop3": dict(kernel="coop", threads_per_block=32, blocks_per_sm=3),
+           "team2": dict(kernel="coop", warps_per_zone=2),
+           "team4": dict(kernel="coop", warps_per_zone=4)}
 
 
 @pytest.mark.parametrize("kernel", list(KERNELS))
