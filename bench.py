@@ -40,15 +40,20 @@ WORKLOAD_DESC = ("13-species alpha chain with self-heating (12 rates, Q~U[1,10])
 # The other workloads of the configuration table, each a sub-entry of the
 # line (name, zones, options of config_entry): the fixed-temperature chain,
 # the 48-species network at its full 262,144 zones, and the 128-species
-# self-heating network on a seeded prefix of its zones (its full 131,072
-# zones take about 1.8e17 flops, a day and a half at the FP64 peak), with a
-# watchdog.  The sensitivity workload is the "adjoint" entry.
+# self-heating network on a seeded 1,024-zone prefix of its zones, with a
+# watchdog (by default), or at its full 131,072 zones ("cfg4_full", about
+# eight minutes).  The 128-species network runs two warps per zone: on the
+# prefix one warp gave 170 zone-burns/s, two 275, four 86.  The sensitivity
+# workload is the "adjoint" entry.
+CFG4_LAUNCH = dict(kernel="coop", warps_per_zone=2)
 CONFIG_TABLE = {
     "cfg0": ("chain13", None, dict(cpu_zones=4096)),
     "cfg2": ("net48", None, dict(cpu_zones=256)),
     "cfg4": ("net128_heat", 1024, dict(cpu_zones=16, plain_zones=0, steps=1, warmup=0,
-                                       budget_s=60.0, launch=dict(kernel="coop"),
+                                       budget_s=60.0, launch=CFG4_LAUNCH,
                                        full_zones=131072)),
+    "cfg4_full": ("net128_heat", 131072, dict(cpu_zones=0, plain_zones=0, steps=1, warmup=0,
+                                              launch=CFG4_LAUNCH)),
 }
 
 
@@ -379,11 +384,20 @@ def run_native(args):
     adj = None
     if args.adjoint:
         adj = adjoint_bench(nb, torch, dev, flush, metrics)
+    adj_cfg = {}
+    if args.cfg4_adjoint:
+        # the 128-species network's adjoint over all 600 multipliers on an
+        # 8192-zone subset: every state on the tape (stride 1), so the
+        # forward may run two warps per zone; zones past 4000 steps (the
+        # runaways) end TAPE_FULL and get no gradient
+        adj_cfg["cfg4"] = adjoint_bench(nb, torch, dev, flush, metrics, repeats=1,
+                                        name="net128_heat", Z=8192, max_steps=4000, stride=1,
+                                        launch=CFG4_LAUNCH, full_tape=False)
     multi = multi_bench(nb, torch, dev, flush) if args.multi else None
     configs = {}
     for cname in [c for c in args.configs.split(",") if c]:
         name, Zc, kw = CONFIG_TABLE[cname]
-        sp = min(args.sample_parity, 32) if cname == "cfg4" else args.sample_parity
+        sp = min(args.sample_parity, 32) if cname.startswith("cfg4") else args.sample_parity
         configs[cname] = config_entry(nb, torch, dev, flush, metrics, name, Zc,
                                       sample_parity=sp, **kw)
 
@@ -419,6 +433,8 @@ def run_native(args):
             "events": ops["events"]}
     if adj is not None:
         line["adjoint"] = adj
+    if adj_cfg:
+        line["adjoint_configs"] = adj_cfg
     if multi is not None:
         line["multi_network"] = multi
     if parity is not None:
@@ -534,25 +550,28 @@ def config_entry(nb, torch, dev, flush, metrics, name, Z=None, steps=3, warmup=1
     return entry
 
 
-def adjoint_bench(nb, torch, dev, flush, metrics, repeats=3) -> dict:
-    """Adjoint gradients/s: the 48-species sensitivity workload, 6 cotangents
-    per zone (energy + the 5 largest final abundances), forward with tape
-    plus reverse sweep (which recomputes the checkpointed blocks), timed
-    `repeats` times, with the FP64 roofline of the reverse kernel."""
-    name = "net48_adjoint"
-    net, z, s = gen.problem(name)
+def adjoint_bench(nb, torch, dev, flush, metrics, repeats=3, name="net48_adjoint", Z=None,
+                  max_steps=4000, stride=16, launch=None, full_tape=True) -> dict:
+    """Adjoint gradients/s: the sensitivity workload (by default the
+    48-species one), 6 cotangents per zone (energy + the 5 largest final
+    abundances), forward with tape plus reverse sweep (which recomputes the
+    checkpointed blocks at stride > 1), timed `repeats` times, with the FP64
+    roofline of the reverse kernel.  A zone that needs more than max_steps
+    steps ends TAPE_FULL and gets no gradient (counted)."""
+    net, z, s = gen.problem(name, Z)
     Z = z["T9"].shape[0]
     nc = nb.Network(net)
     info = nc.info()
     Y0 = torch.from_numpy(z["Y"]).to(dev)
     T9 = torch.from_numpy(z["T9"]).to(dev)
     rho = torch.from_numpy(z["rho"]).to(dev)
-    # one warp per zone for this network, forward and reverse (a checkpointed
-    # tape is recomputed in the arithmetic that recorded it)
+    # one warp per zone for a large network, forward and reverse (a
+    # checkpointed tape is recomputed in the arithmetic that recorded it)
     fk = "coop" if info["n_state"] >= 24 else "persistent"
     kname = "k_adjoint_coop" if fk == "coop" else "k_adjoint"
-    tape = nb.Tape(nc, Z, 4000)
-    fw = nb.burn(nc, Y0, T9, rho, s["t_end"], s["rtol"], s["atol"], tape=tape, kernel=fk)
+    fl = dict(kernel=fk) if launch is None else dict(launch)
+    tape = nb.Tape(nc, Z, max_steps, stride)
+    fw = nb.burn(nc, Y0, T9, rho, s["t_end"], s["rtol"], s["atol"], tape=tape, **fl)
     torch.cuda.synchronize()
     Yf = fw.Y.cpu().numpy()
     top = gen.largest_species(Yf, 5)
@@ -571,7 +590,7 @@ def adjoint_bench(nb, torch, dev, flush, metrics, repeats=3) -> dict:
         flush.fill_(3.0 + k)
         a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         a.record()
-        fw = nb.burn(nc, Y0, T9, rho, s["t_end"], s["rtol"], s["atol"], tape=tape, kernel=fk)
+        fw = nb.burn(nc, Y0, T9, rho, s["t_end"], s["rtol"], s["atol"], tape=tape, **fl)
         b.record()
         nb.adjoint(nc, tape, gYd, gEd)
         c.record()
@@ -580,27 +599,32 @@ def adjoint_bench(nb, torch, dev, flush, metrics, repeats=3) -> dict:
         rev.append(b.elapsed_time(c))
     fwd_ms, adj_ms = statistics.mean(fwd), statistics.mean(rev)
     # the same with every state on the tape (stride 1): no recomputation
-    full = nb.Tape(nc, Z, 4000, 1)
-    nb.burn(nc, Y0, T9, rho, s["t_end"], s["rtol"], s["atol"], tape=full, kernel=fk)
-    flush.fill_(9.0)
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record()
-    nb.adjoint(nc, full, gYd, gEd)
-    b.record()
-    torch.cuda.synchronize()
-    full_ms = a.elapsed_time(b)
-    del full
+    full_ms = None
+    if full_tape and stride != 1:
+        full = nb.Tape(nc, Z, max_steps, 1)
+        nb.burn(nc, Y0, T9, rho, s["t_end"], s["rtol"], s["atol"], tape=full, **fl)
+        flush.fill_(9.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        nb.adjoint(nc, full, gYd, gEd)
+        b.record()
+        torch.cuda.synchronize()
+        full_ms = a.elapsed_time(b)
+        del full
     st = fw.status.cpu().numpy()
     cnt = fw.counters.cpu().numpy()
-    steps = int(cnt[:, 0].sum())
+    ok = st == 0                  # the zones that get gradients
+    steps = int(cnt[ok, 0].sum())
     flops = metrics.adjoint_ops(info, steps, K, net.self_heating)
     achieved = flops / (adj_ms * 1e-3) / 1e12
-    return {"workload": "48 species / 180 rates, 16384 zones, T9 log-U[0.3,6], "
-                        "rho log-U[1e4,1e9], t_end 1e-2, 6 cotangents per zone",
-            "value": Z * K / ((fwd_ms + adj_ms) * 1e-3), "unit": "gradients/s",
+    return {"workload": workload_desc(name, Z) + ", 6 cotangents per zone",
+            "value": int(ok.sum()) * K / ((fwd_ms + adj_ms) * 1e-3), "unit": "gradients/s",
             "gradient_length": net.R, "forward_ms": fwd_ms, "reverse_ms": adj_ms,
             "repeats": repeats, "forward_ms_each": fwd, "reverse_ms_each": rev,
-            "tape_checkpoint_stride": 16, "zones_ok": int((st == 0).sum()),
+            "tape_checkpoint_stride": stride, "tape_max_steps": max_steps,
+            "zones_ok": int(ok.sum()),
+            "zone_status_counts": {str(k): int(v) for k, v in zip(*np.unique(st, return_counts=True))},
+            "forward_launch": fl,
             "reverse_ms_full_tape": full_ms,
             "forward_kernel": "k_burn_coop" if fk == "coop" else "k_burn_persistent",
             "adjoint_kernel": kname,
@@ -681,6 +705,9 @@ def main():
     p.add_argument("--ref-zones", type=int, default=4096)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--adjoint", action=argparse.BooleanOptionalAction, default=True)
+    p.add_argument("--cfg4-adjoint", action="store_true",
+                   help="add the 128-species network's 8192-zone adjoint over all 600 "
+                        "multipliers (a few minutes)")
     p.add_argument("--multi", action=argparse.BooleanOptionalAction, default=True)
     args = p.parse_args()
     if args.impl == "reference":

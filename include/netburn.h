@@ -332,7 +332,8 @@ int nb_burn_adjoint(nb_net net, void* tape, int32_t K, const double* gY,
  * opt: kernel (NB_KERNEL_PERSISTENT one lane per zone, NB_KERNEL_COOP one
  * warp per zone; at stride above 1 it must be the recording burn's family,
  * else NB_E_TAPE, because the other family's arithmetic would recompute
- * states that differ from the recorded burn's in the last bits),
+ * states that differ from the recorded burn's in the last bits; a tape
+ * recorded with warps_per_zone > 1 is read only at stride 1),
  * threads_per_block (lane kernel at
  * most 128; warp kernel: warps per block x 32, at most 256, default as many
  * as fit in shared memory up to 4), blocks_per_sm, ws_in_shared (0: the

@@ -203,11 +203,14 @@ extern "C" int nb_burn_adjoint_ex(nb_net net, void* tape, int32_t K, const doubl
   // arithmetic of the recording burn, so that the recomputed states are the
   // forward's bits; else one warp per zone from 24 state entries on
   int kernel = o.kernel;
-  if (!opt || kernel == NB_KERNEL_AUTO)
-    kernel = tp->dev.stride > 1 ? tp->family
-                                : (n >= 24 ? NB_KERNEL_COOP : NB_KERNEL_PERSISTENT);
+  const bool recompute = tp->dev.stride > 1;
+  const bool family_ok = tp->family == NB_KERNEL_COOP || tp->family == NB_KERNEL_PERSISTENT;
+  if (!opt || kernel == NB_KERNEL_AUTO) {
+    if (recompute && !family_ok) return NB_E_TAPE;   // recorded by teams of warps
+    kernel = recompute ? tp->family : (n >= 24 ? NB_KERNEL_COOP : NB_KERNEL_PERSISTENT);
+  }
   if (kernel != NB_KERNEL_COOP && kernel != NB_KERNEL_PERSISTENT) return NB_E_ARG;
-  if (tp->dev.stride > 1 && kernel != tp->family) return NB_E_TAPE;
+  if (recompute && kernel != tp->family) return NB_E_TAPE;
   cudaStream_t st = (cudaStream_t)stream;
   std::lock_guard<std::mutex> lk(net->mu);
   const size_t blob_b = (size_t)h.bytes;

@@ -675,7 +675,11 @@ extern "C" int nb_burn_batch(nb_net net, int64_t Z, const double* Y0, const doub
   if (rc || !tp) return rc;
   tp->recZ = Z;
   tp->recorded = 1;
-  tp->family = o.kernel == NB_KERNEL_COOP ? NB_KERNEL_COOP : NB_KERNEL_PERSISTENT;
+  // teams of several warps per zone sum in another order than one warp: a
+  // family of their own, which no adjoint kernel recomputes
+  tp->family = o.kernel != NB_KERNEL_COOP ? NB_KERNEL_PERSISTENT
+               : o.warps_per_zone > 1    ? NB_KERNEL_COOP + 8 * o.warps_per_zone
+                                         : NB_KERNEL_COOP;
   tp->t_end = t_end; tp->rtol = rtol; tp->atol = atol;
   tp->has_lnm = ln_mult != nullptr;
   tp->lnm_per_zone = P.lnm_per_zone;

@@ -136,6 +136,19 @@ def test_checkpointed_tape_recomputes_in_the_recording_arithmetic():
         d = nb.adjoint(nc, tape1, gY, kernel=other)[0]
         assert torch.equal(a, c)
         assert torch.allclose(c, d, rtol=1e-7, atol=1e-10 * float(c.abs().max()))
+    # a burn by teams of two warps sums in its own order: no adjoint kernel
+    # recomputes its blocks, and its every-state tape is read as usual
+    tape = nb.Tape(nc, 8, 4000, 16)
+    nb.burn(nc, *args, s["t_end"], s["rtol"], s["atol"], tape=tape, kernel="coop",
+            warps_per_zone=2)
+    for k in ("auto", "coop", "persistent"):
+        with pytest.raises(nb.NetburnError):
+            nb.adjoint(nc, tape, gY, kernel=k)
+    tape1 = nb.Tape(nc, 8, 4000, 1)
+    nb.burn(nc, *args, s["t_end"], s["rtol"], s["atol"], tape=tape1, kernel="coop",
+            warps_per_zone=2)
+    e = nb.adjoint(nc, tape1, gY)[0]
+    assert torch.allclose(e, c, rtol=1e-6, atol=1e-9 * float(c.abs().max()))
 
 
 def test_dot_product_identity():
