@@ -350,14 +350,16 @@ __device__ __forceinline__ void solve_M(const WNetT<W>& t, const CWS& w, const C
   for (int k = t.n - 1; k >= 0; --k) {
     const int pk = t.perm[k];
     const double xk = v[pk] * w.lu[g.piv[k].dslot];
-    t.sync();
-    if (t.lane == 0) v[pk] = xk;
     for (int e = t.ucol_ptr[k] + t.lane; e < t.ucol_ptr[k + 1]; e += W) {
       const int r = t.ucol_t[e];
       v[r] = fma(-w.lu[t.ucol_s[e]], xk, v[r]);
     }
     t.sync();
+    // every thread has read v[pk]; no later column reads or updates it
+    // (their targets lie above them in the pivot order)
+    if (t.lane == 0) v[pk] = xk;
   }
+  t.sync();
 }
 
 // v <- M^-T v with the factored w.lu (the adjoint): U^T column by column
@@ -370,14 +372,16 @@ __device__ __forceinline__ void solve_MT(const WNetT<W>& t, const CV& lu, const 
     const Pivot p = g.piv[k];
     const int pk = t.perm[k];
     const double xk = v[pk] * lu[p.dslot];
-    t.sync();
-    if (t.lane == 0) v[pk] = xk;
     for (int u = p.ubeg + t.lane; u < p.uend; u += W) {
       const int r = t.utgt[u];
       v[r] = fma(-lu[g.uslot[u]], xk, v[r]);
     }
     t.sync();
+    // every thread has read v[pk]; no later row reads or updates it (their
+    // targets lie below them in the pivot order)
+    if (t.lane == 0) v[pk] = xk;
   }
+  t.sync();
   for (int k = t.n - 1; k >= 0; --k) {
     const double xk = v[t.perm[k]];
     for (int e = t.lrow_ptr[k] + t.lane; e < t.lrow_ptr[k + 1]; e += W) {
