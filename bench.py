@@ -90,6 +90,17 @@ def launch_shape(launch, variant):
                       (launch.get("blocks_per_sm", 0) or 1), variant)
 
 
+def coop_shape(launch):
+    """threads per block, blocks per SM and warps per zone of a warp-kernel
+    launch (which instance runs and how many share an SM); None for the other
+    kernels, whose entries do not check the shape."""
+    if launch.get("kernel") != "coop":
+        return None
+    return "coop,%d,%d,%d" % (launch.get("threads_per_block", 0) or 0,
+                              launch.get("blocks_per_sm", 0) or 0,
+                              launch.get("warps_per_zone", 0) or 0)
+
+
 def profiled_traffic(kernel, Z, shape, workload="chain13_heat"):
     """DRAM bytes per launch from the committed ncu summary of this kernel on
     this workload, or None when the kernel sources, the zone count or the
@@ -397,7 +408,7 @@ def run_native(args):
     configs = {}
     for cname in [c for c in args.configs.split(",") if c]:
         name, Zc, kw = CONFIG_TABLE[cname]
-        sp = min(args.sample_parity, 32) if cname.startswith("cfg4") else args.sample_parity
+        sp = args.sample_parity
         configs[cname] = config_entry(nb, torch, dev, flush, metrics, name, Zc,
                                       sample_parity=sp, **kw)
 
@@ -510,7 +521,7 @@ def config_entry(nb, torch, dev, flush, metrics, name, Z=None, steps=3, warmup=1
              "roofline": {"bound": "alu", "achieved": achieved,
                           "peak": metrics.FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                           "frac": achieved / metrics.FP64_PEAK_TFLOPS,
-                          "traffic": profiled_traffic(kname, Z, None, workload=name),
+                          "traffic": profiled_traffic(kname, Z, coop_shape(launch), workload=name),
                           "kernel": kname, "flops_per_launch": ops["flops"],
                           "algorithmic_bytes_per_launch": int(Z * zone_bytes(net.N)),
                           "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2070 MHz"},
