@@ -204,19 +204,20 @@ def sampled_parity(name, net, z, s, out, n) -> dict:
     return rep
 
 
-def cpu_baseline(name: str, Z_sample: int, zone_offset: int = 0) -> dict:
-    """The oracle, as it stands, on a bounded sample of the workload."""
+def cpu_baseline(name: str, Z_sample: int, zone_offset: int = 0, threads: int = 0) -> dict:
+    """The oracle, as it stands, on a bounded sample of the workload (all host
+    cores, or `threads` of them)."""
     import oracle
     net, z, s = gen.problem(name, zone_offset + Z_sample)
     z = {k: v[zone_offset:] for k, v in z.items()}
     t0 = time.perf_counter()
     out = oracle.burn(net, z["Y"], z["T9"], z["rho"], s["t_end"], s["rtol"], s["atol"],
-                      zeta=z.get("zeta"))
+                      zeta=z.get("zeta"), threads=threads)
     dt = time.perf_counter() - t0
     return {"value": Z_sample / dt, "unit": "zone-burns/s", "cores": int(out["threads"]),
             "kind": "oracle", "seconds": dt,
             "sample": f"first {Z_sample} zones of {name} (i.i.d. seeded zones), "
-                      f"all host cores"}
+                      + ("all host cores" if not threads else f"{threads} host core(s)")}
 
 
 def run_reference(args):
@@ -388,6 +389,10 @@ def run_native(args):
     if not args.no_cpu_baseline:
         base = cpu_baseline(workload, args.cpu_zones)
         base.pop("seconds", None)
+        # and on one core, on a smaller sample of the same zones
+        one = cpu_baseline(workload, max(64, args.cpu_zones // 16), threads=1)
+        one.pop("seconds", None)
+        base["one_core"] = one
     parity = None
     if args.sample_parity:
         parity = sampled_parity(workload, net_spec, z, s, out, args.sample_parity)

@@ -235,7 +235,7 @@ def burn(net, Y0, T9, rho, t_end, rtol, atol, ln_mult=None, threads=0, zeta=None
          **opts):
     """Burn Z zones.  t_end is a number or a per-zone array [Z]; zeta None or
     the per-zone plasma parameters [Z] for screening.  Returns
-    dict(Y, T9, E, counters [Z, 8], status, threads)."""
+    dict(Y, T9, E, counters [Z, 9], status, threads)."""
     net = _net(net)
     lib = _load()
     Y0 = _f64(np.atleast_2d(Y0))
