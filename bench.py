@@ -108,14 +108,21 @@ def profiled_traffic(kernel, Z, shape, workload="chain13_heat"):
     path = os.path.join(ROOT, "profiles", kernel + "_" + workload + ".md")
     if not os.path.exists(path):
         return None
-    kv = {}
+    # one block of "key: value" lines per profiled launch shape, each opened
+    # by a line that starts with "machine-readable"
+    blocks, kv = [], None
     for line in open(path):
-        if ":" in line and not line.startswith(("|", "#", " ")):
+        if line.startswith("machine-readable"):
+            kv = {}
+            blocks.append(kv)
+        elif kv is not None and ":" in line and not line.startswith(("|", "#", " ")):
             k, v = line.split(":", 1)
             kv[k.strip()] = v.strip()
-    if (kv.get("source_hash") == kernel_source_hash() and kv.get("zones") == str(Z)
-            and (shape is None or kv.get("launch") == shape) and "dram_bytes_per_launch" in kv):
-        return int(kv["dram_bytes_per_launch"])
+    for kv in blocks:
+        if (kv.get("source_hash") == kernel_source_hash() and kv.get("zones") == str(Z)
+                and (shape is None or kv.get("launch") == shape)
+                and "dram_bytes_per_launch" in kv):
+            return int(kv["dram_bytes_per_launch"])
     return None
 
 
@@ -711,7 +718,8 @@ def main():
     p.add_argument("--threads-per-block", type=int, default=0)
     p.add_argument("--ws-in-shared", type=int, default=-1)
     p.add_argument("--specialize", type=int, default=None,
-                   help="-1 generic kernel, 0 automatic, 1..3 specialised variant")
+                   help="-1 generic kernel, 0 automatic, 1..3 specialised storage variant, "
+                        "4..6 the same for three 128-thread blocks per SM")
     p.add_argument("--kernel", default="persistent", choices=["persistent", "coop"],
                    help="the main workload's kernel (coop: one warp per zone); "
                         "persistent lets the autotuner choose")
