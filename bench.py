@@ -718,8 +718,7 @@ def main():
     p.add_argument("--threads-per-block", type=int, default=0)
     p.add_argument("--ws-in-shared", type=int, default=-1)
     p.add_argument("--specialize", type=int, default=None,
-                   help="-1 generic kernel, 0 automatic, 1..3 specialised storage variant, "
-                        "4..6 the same for three 128-thread blocks per SM")
+                   help="-1 generic kernel, 0 automatic, 1..3 specialised variant")
     p.add_argument("--kernel", default="persistent", choices=["persistent", "coop"],
                    help="the main workload's kernel (coop: one warp per zone); "
                         "persistent lets the autotuner choose")

@@ -187,11 +187,8 @@ typedef struct {
                                the network is small enough for it and it
                                builds, else the generic kernel; -1 always the
                                generic kernel; 1..3 the specialised kernel
-                               with that storage variant, 4..6 the storage
-                               variants 1..3 built for three blocks of at
-                               most 128 threads per SM (registers capped at
-                               168; NB_E_ARG with threads_per_block > 128)
-                               (NB_E_COMPILE when it cannot be built).  Ignored with ws_in_shared
+                               with that storage variant (NB_E_COMPILE when it
+                               cannot be built).  Ignored with ws_in_shared
                                > 0 and by nb_burn_batch_noalloc (always the
                                generic kernel). */
   const double* t_end_zone; /* [Z] device array of per-zone end times, or NULL
@@ -427,8 +424,7 @@ int nb_burn_multi(int32_t n_sets, const nb_burn_set* sets, double t_end, double 
  * the same bits.
  *  variant  0: chosen from the network's sizes; 1: all Newton-loop arrays of
  *           a zone in registers; 2: as 1 with the LU in the workspace;
- *           3: only x, d, f in registers; 4..6: variants 1..3 built for
- *           three 128-thread blocks per SM (registers capped at 168).
+ *           3: only x, d, f in registers.
  *  log      NULL or a host buffer of log_bytes for the compiler's log
  *           (NUL-terminated, truncated to fit).
  * Synchronous; compiling takes seconds.  NB_E_COMPILE on failure.  A kernel

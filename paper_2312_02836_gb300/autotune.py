@@ -41,9 +41,7 @@ GENERIC_CANDIDATES = (
 
 SPECIALIZED_CANDIDATES = tuple(
     dict(specialize=v, threads_per_block=tpb, blocks_per_sm=bps)
-    for v in (1, 2, 3) for tpb, bps in ((64, 1), (128, 1), (128, 2), (256, 1))) + tuple(
-    # the same storage variants with registers capped for three blocks per SM
-    dict(specialize=v, threads_per_block=128, blocks_per_sm=3) for v in (4, 5, 6))
+    for v in (1, 2, 3) for tpb, bps in ((64, 1), (128, 1), (128, 2), (256, 1)))
 
 # one warp per zone, its Newton-loop arrays in shared memory (large networks)
 COOP_CANDIDATES = (

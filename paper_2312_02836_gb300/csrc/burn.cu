@@ -326,7 +326,7 @@ static void copy_log(const std::string& s, char* log, int64_t cap) {
 }
 
 extern "C" int nb_net_specialize(nb_net net, int32_t variant, char* log, int64_t log_bytes) {
-  if (!net || variant < 0 || variant > 6) return NB_E_ARG;
+  if (!net || variant < 0 || variant > 3) return NB_E_ARG;
   std::lock_guard<std::mutex> lk(net->mu);
   const int v = resolve_variant(net->h, variant);
   const void* fn = nullptr;
@@ -345,7 +345,7 @@ static int host_blob(const nb_topology* T, const double* coeffs, std::vector<uin
 
 extern "C" int nb_specialize_source(const nb_topology* T, const double* coeffs,
                                     int32_t variant, char* buf, int64_t cap, int64_t* len) {
-  if (!len || variant < 0 || variant > 6) return NB_E_ARG;
+  if (!len || variant < 0 || variant > 3) return NB_E_ARG;
   std::vector<uint8_t> blob;
   int rc = host_blob(T, coeffs, &blob);
   if (rc) return rc;
@@ -358,7 +358,7 @@ extern "C" int nb_specialize_source(const nb_topology* T, const double* coeffs,
 
 extern "C" int nb_specialize_compile(const nb_topology* T, const double* coeffs,
                                      int32_t variant, char* log, int64_t log_bytes) {
-  if (variant < 0 || variant > 6) return NB_E_ARG;
+  if (variant < 0 || variant > 3) return NB_E_ARG;
   std::vector<uint8_t> blob;
   int rc = host_blob(T, coeffs, &blob);
   if (rc) return rc;
@@ -509,9 +509,7 @@ static int launch_burn(nb_net net, BurnParams& P, const nb_options& o,
   // the network qualifies and it builds
   const void* spec_fn = nullptr;
   int spec_variant = 0;
-  if (o.specialize > 6 || o.specialize < -1) return NB_E_ARG;
-  // variants 4..6 are built for blocks of at most 128 threads
-  if (o.specialize > 3 && tpb > 128) return NB_E_ARG;
+  if (o.specialize > 3 || o.specialize < -1) return NB_E_ARG;
   if (o.kernel == NB_KERNEL_PERSISTENT && o.ws_in_shared <= 0 && o.specialize >= 0) {
     if (o.specialize > 0) {
       int rc = spec_get(net, o.specialize, &spec_fn);

@@ -84,7 +84,7 @@ void emit_pairs(Out& o, int beg, int end, F term) {
 }  // namespace
 
 int resolve_variant(const BlobHeader& h, int variant) {
-  if (variant >= 1 && variant <= 6) return variant;
+  if (variant >= 1 && variant <= 3) return variant;
   const int vec = 7 * h.n;
   if (vec + h.nnz <= 160) return 1;
   if (vec <= 160) return 2;
@@ -101,10 +101,6 @@ bool specialize_auto_ok(const BlobHeader& h) {
 std::string specialized_source(const std::vector<uint8_t>& blob, int variant) {
   const BlobHeader& h = *reinterpret_cast<const BlobHeader*>(blob.data());
   variant = resolve_variant(h, variant);
-  // variants 4..6: storage variants 1..3 built for three 128-thread blocks
-  // per SM (registers capped at 168)
-  const bool dense = variant > 3;
-  if (dense) variant -= 3;
   const int n = h.n, N = h.N, R = h.R, nnz = h.nnz, nd = h.nd;
   const bool sh = h.self_heating != 0;
   const double* coef = arr<double>(blob, h.o_coef);
@@ -398,11 +394,11 @@ std::string specialized_source(const std::vector<uint8_t>& blob, int variant) {
   o("}\n\n}  // namespace nb\n\n");
 
   // ---- kernel
-  o("extern \"C\" __global__ void __launch_bounds__(%s) nb_spec_burn(nb::BurnParams P) {\n"
+  o("extern \"C\" __global__ void __launch_bounds__(256, 1) nb_spec_burn(nb::BurnParams P) {\n"
     "  using namespace nb;\n  GNet t;\n  const int lane = threadIdx.x & 31;\n"
     "  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;\n"
     "  double* base = P.ws + warp * (long long)%d * WS_LANES + lane;\n  GWS w;\n",
-    dense ? "128, 3" : "256, 1", h.lane_doubles);
+    h.lane_doubles);
   auto lv = [&](const char* name, int off) {
     o("  w.%s.p = base + %d * WS_LANES;\n", name, off);
   };

@@ -36,7 +36,7 @@ struct nb_net_s {
     cudaLibrary_t lib = nullptr;
     cudaKernel_t kern = nullptr;
     std::string log;
-  } spec[7];
+  } spec[4];
   int last_spec = 0;   // variant the last burn ran (0 generic)
   std::mutex mu;
 };

@@ -40,11 +40,6 @@ def test_source_spells_out_the_network():
     assert "double lu[" in nb.specialized_source(net, 1)
     assert "LV lu;" in nb.specialized_source(net, 2)
     assert "LV psi, iw, xp, tmp;" in nb.specialized_source(net, 3)
-    # variants 4..6: variants 1..3 built for three 128-thread blocks per SM
-    for v in (1, 2, 3):
-        a, b = nb.specialized_source(net, v), nb.specialized_source(net, v + 3)
-        assert "__launch_bounds__(256, 1)" in a and "__launch_bounds__(128, 3)" in b
-        assert a.replace("__launch_bounds__(256, 1)", "__launch_bounds__(128, 3)") == b
     # fixed temperature: no derivative factors, rates kept for the whole zone
     src0 = nb.specialized_source(gen.network("chain13"), 1)
     assert "rate_dlog" not in src0 and "LV k;" in src0
