@@ -268,13 +268,23 @@ def run_native(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     workload = args.workload
     Z = args.zones or gen.CONFIGS[workload]["Z"]
-    net_spec, zall, s = gen.problem(workload, Z * ws)
+    Z_job = Z * ws
+    net_spec, zall, s = gen.problem(workload, Z_job)
     if args.t_end is not None:
         s["t_end"] = args.t_end
     from paper_2312_02836_gb300.parallel import max_over_ranks, shard
-    lo, hi = shard(Z * ws, ws, rank)           # weak scaling: Z zones per rank
-    z = {k: np.ascontiguousarray(v[lo:hi]) for k, v in zall.items()}
     netc = nb.Network(net_spec)
+    # weak scaling: Z zones per rank on average, the ranges balanced by each
+    # zone's predicted cost (every rank predicts all zones, the same numbers)
+    cost = None
+    if ws > 1:
+        ca = {k: torch.from_numpy(v).to(dev) for k, v in zall.items()}
+        cost = nb.zone_costs(netc, ca["Y"], ca["T9"], ca["rho"], s["t_end"], s["rtol"],
+                             s["atol"], zeta=ca.get("zeta")).cpu().numpy()
+        del ca
+    lo, hi = shard(Z_job, ws, rank, cost)
+    z = {k: np.ascontiguousarray(v[lo:hi]) for k, v in zall.items()}
+    Z = hi - lo
     info = netc.info()
     Y0 = torch.from_numpy(z["Y"]).to(dev)
     T9 = torch.from_numpy(z["T9"]).to(dev)
@@ -329,18 +339,18 @@ def run_native(args):
     barrier()
     clk = clocks.stop() if clocks else None
     ms = [a.elapsed_time(b) for a, b in ev]
-    mean_ms = max_over_ranks(statistics.mean(ms), dev)
+    local_ms = statistics.mean(ms)          # this rank's launch (its roofline)
+    mean_ms = max_over_ranks(local_ms, dev)
     variant = netc.info()["last_specialized"]
     kname = ("k_burn_coop" if launch.get("kernel") == "coop" else
              "nb_spec_burn" if variant else "k_burn_persistent")
     counters = out.counters.cpu().numpy()
     status = out.status.cpu().numpy()
     ops = metrics.burn_ops(info, counters, net_spec.self_heating)
-    value = Z * ws / (mean_ms * 1e-3)
+    value = Z_job / (mean_ms * 1e-3)
 
-    if rank != 0:
-        return
-    # ---- end to end through the host-pointer C entry point (pinned buffers)
+    # ---- end to end through the host-pointer C entry point (pinned buffers),
+    # every rank its own zones, the slowest rank's time
     N = net_spec.N
     hY0 = torch.from_numpy(z["Y"]).pin_memory().numpy()
     hT9 = torch.from_numpy(z["T9"]).pin_memory().numpy()
@@ -363,8 +373,11 @@ def run_native(args):
         e2e_t.append(time.perf_counter() - t0)
     if e2e_t:
         assert np.array_equal(hout["Y"], out.Y.cpu().numpy())
+        e2e_s = max_over_ranks(statistics.mean(e2e_t), dev)
     h2d = hY0.nbytes + hT9.nbytes + hrho.nbytes
     d2h = sum(a.nbytes for a in hout.values())
+    if rank != 0:
+        return
 
     # ---- plain one-thread-per-zone launch, same inputs and tolerances
     plain_ms = []
@@ -379,7 +392,7 @@ def run_native(args):
     plain_equal = bool(np.array_equal(out.Y.cpu().numpy(), hout["Y"])) if plain_ms and e2e_t else None
 
     # ---- roofline of the burn kernel (one launch per step)
-    achieved = ops["flops"] / (mean_ms * 1e-3) / 1e12
+    achieved = ops["flops"] / (local_ms * 1e-3) / 1e12
     peak = metrics.FP64_PEAK_TFLOPS
     traffic = profiled_traffic(kname, Z, launch_shape(launch, variant))
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -429,7 +442,7 @@ def run_native(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD_DESC if workload == WORKLOAD else
-                       workload_desc(workload, Z), "zones_per_gpu": Z,
+                       workload_desc(workload, Z_job // ws), "zones_per_gpu": Z_job // ws,
                        "l2": "256 MiB buffer written between timed steps (L2 flush)",
                        "kernel": ("persistent warp-per-zone, device work queue, arrays in "
                                   "shared memory" if launch.get("kernel") == "coop" else
@@ -440,7 +453,7 @@ def run_native(args):
                        "autotune_ms": None if tune_ms is None else
                        [[c, round(m, 2)] for c, m in tune_ms]},
             "roofline": roofline, "cpu_baseline": base,
-            "e2e": None if not e2e_t else {"value": Z / statistics.mean(e2e_t), "unit": "zone-burns/s",
+            "e2e": None if not e2e_t else {"value": Z_job / e2e_s, "unit": "zone-burns/s",
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                     "path": "nb_burn_batch_host (pinned host buffers, copies inside)"},
             # per step: the burn kernel, plus the longest-first pre-pass
