@@ -387,13 +387,16 @@ int nb_burn_batch_noalloc(nb_net net, int64_t Z, const double* Y0,
  * pointers, [Z, N] with that network's N), in one persistent launch whose
  * device queue spans all of them: a few expensive zones of a large network
  * and many cheap zones of a small one share the GPU's lanes.  Sets of larger
- * networks are claimed first.  Every zone follows the generic kernel, bit
- * for bit the result nb_burn_batch gives it.  t_end, rtol and atol are
- * common; t_end_zone (per set, may be NULL) overrides t_end per zone.  From
- * opt: max_attempts, threads_per_block (<= 128), blocks_per_sm and
- * time_budget_s; no tape, no specialised kernel.  All networks must live on
- * the current device.  The first set's network lends its device workspace:
- * do not burn with it concurrently.  Asynchronous on stream. */
+ * networks are claimed first, and within a set (schedule 1, the default)
+ * the zones longest first by their starting step, as nb_burn_batch orders
+ * them.  Every zone follows the generic kernel, bit for bit the result
+ * nb_burn_batch gives it.  t_end, rtol and atol are common; t_end_zone (per
+ * set, may be NULL) overrides t_end per zone.  From opt: max_attempts,
+ * threads_per_block (<= 128), blocks_per_sm, schedule and time_budget_s; no
+ * tape, no specialised kernel.  All networks must live on the current
+ * device.  The first set's network lends its device workspace and its
+ * scheduling buffers: do not burn with it concurrently.  Asynchronous on
+ * stream. */
 #define NB_MULTI_MAX_SETS 12
 typedef struct {
   nb_net net;

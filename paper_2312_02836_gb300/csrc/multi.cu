@@ -10,6 +10,7 @@
 // zone it claimed (from global memory, through L1) and runs the generic
 // integrator, so every zone gives the same bits as a single-network burn.
 #include <cuda_runtime.h>
+#include <cub/device/device_segmented_radix_sort.cuh>
 
 #include <algorithm>
 #include <cmath>
@@ -34,6 +35,7 @@ struct MultiParams {
   int lane_doubles;
   unsigned long long* queue;
   unsigned long long budget_ns;
+  const int32_t* order;                   // claim position -> claim index, or null
 };
 // passed by value as the kernel's parameter block (the classic 4 KB limit)
 static_assert(sizeof(MultiParams) <= 4000, "MultiParams exceeds the kernel parameter space");
@@ -58,9 +60,11 @@ __global__ void __launch_bounds__(128, 1) k_burn_multi(const __grid_constant__ M
       if (!active && !retired) {
         const unsigned long long c = base + __popc(need & ((1u << lane) - 1u));
         if (c < (unsigned long long)total) {
+          // the order keeps every position within its own set's range
+          const long long ci = M.order ? (long long)M.order[c] : (long long)c;
           m = 0;
-          while (m + 1 < M.n && (long long)c >= M.off[m + 1]) ++m;
-          s.z = (long long)c - M.off[m];
+          while (m + 1 < M.n && ci >= M.off[m + 1]) ++m;
+          s.z = ci - M.off[m];
           active = true;
           fresh = true;
         } else {
@@ -95,6 +99,31 @@ __global__ void __launch_bounds__(128, 1) k_burn_multi(const __grid_constant__ M
         active = false;
       }
     }
+  }
+}
+
+// Scheduling pre-pass: every zone's starting step h0 (the integrator's own
+// start-up) as the key of its claim index; zones that finish in start-up go
+// last.  Sorted within each set, the keys give each set's zones longest
+// first, so a warp's lanes get zones of alike length.
+__global__ void __launch_bounds__(128, 1) k_multi_estimate(const __grid_constant__ MultiParams M,
+                                                          double* key, int32_t* idx) {
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  double* lane_base = M.ws + warp * (long long)M.lane_doubles * WS_LANES + lane;
+  const long long total = M.off[M.n];
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < total; c += stride) {
+    int m = 0;
+    while (m + 1 < M.n && c >= M.off[m + 1]) ++m;
+    const BurnParams& P = M.p[m];
+    const Net t = make_net(P.blob);
+    WS w = make_ws(t, lane_base);
+    Zone s;
+    s.z = c - M.off[m];
+    const bool done = zone_init(t, s, w, P);
+    key[c] = done ? 1e300 : s.h;
+    idx[c] = (int32_t)c;
   }
 }
 
@@ -173,6 +202,34 @@ extern "C" int nb_burn_multi(int32_t n_sets, const nb_burn_set* sets, double t_e
   if (rc) return rc;
   M.ws = host->ws;
   M.queue = host->queue;
+  M.order = nullptr;
+  if (o.schedule == 1 && total > 1 && total <= 0x7fffffffLL) {
+    // longest first within each set (segments at the sets' claim offsets)
+    int seg[NB_MULTI_MAX_SETS + 1];
+    for (int k = 0; k <= n_sets; ++k) seg[k] = (int)M.off[k];
+    size_t temp = 0;
+    CK(cub::DeviceSegmentedRadixSort::SortPairs(
+        nullptr, temp, (const double*)nullptr, (double*)nullptr, (const int32_t*)nullptr,
+        (int32_t*)nullptr, (int)total, n_sets, seg, seg + 1, 0, 64, st));
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t kb = al((size_t)total * 8), ib = al((size_t)total * 4);
+    const size_t sb = al(sizeof(seg));
+    rc = nb::ensure((void**)&host->sched, &host->sched_bytes, 2 * kb + 2 * ib + sb + al(temp));
+    if (rc) return rc;
+    unsigned char* base = host->sched;
+    double* k_in = (double*)base;
+    double* k_out = (double*)(base + kb);
+    int32_t* i_in = (int32_t*)(base + 2 * kb);
+    int32_t* i_out = (int32_t*)(base + 2 * kb + ib);
+    int* d_seg = (int*)(base + 2 * kb + 2 * ib);
+    void* tmp = base + 2 * kb + 2 * ib + sb;
+    CK(cudaMemcpyAsync(d_seg, seg, sizeof(seg), cudaMemcpyHostToDevice, st));
+    k_multi_estimate<<<(unsigned)blocks, tpb, 0, st>>>(M, k_in, i_in);
+    CK(cudaGetLastError());
+    CK(cub::DeviceSegmentedRadixSort::SortPairs(tmp, temp, k_in, k_out, i_in, i_out, (int)total,
+                                                n_sets, d_seg, d_seg + 1, 0, 64, st));
+    M.order = i_out;
+  }
   CK(cudaMemsetAsync(host->queue, 0, sizeof(unsigned long long), st));
   k_burn_multi<<<(unsigned)blocks, tpb, 0, st>>>(M);
   CK(cudaGetLastError());
