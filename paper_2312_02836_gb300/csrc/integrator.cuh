@@ -344,31 +344,12 @@ struct APRate {
   double lam, l_ag, via_p, frac;
 };
 
-// A product and a sum the compiler may not fuse into an FMA: the effective
-// rate's few products and sums are spelled out (fma, or these), so that the
-// kernel generated for a network and the generic one, each compiled with
-// contraction allowed, round them alike.
-NB_HD __forceinline__ double mul_nc(double a, double b) {
-#ifdef __CUDA_ARCH__
-  return __dmul_rn(a, b);
-#else
-  return a * b;
-#endif
-}
-NB_HD __forceinline__ double add_nc(double a, double b) {
-#ifdef __CUDA_ARCH__
-  return __dadd_rn(a, b);
-#else
-  return a + b;
-#endif
-}
-
 NB_HD __forceinline__ APRate ap_rate(double e_ag, double e_ap, double e_pg, double e_pa) {
   APRate a;
   a.l_ag = exp_tang(e_ag);
-  a.frac = 1.0 / add_nc(1.0, exp_tang(e_pa - e_pg));
-  a.via_p = mul_nc(exp_tang(e_ap), a.frac);
-  a.lam = add_nc(a.l_ag, a.via_p);
+  a.frac = 1.0 / (1.0 + exp_tang(e_pa - e_pg));
+  a.via_p = exp_tang(e_ap) * a.frac;
+  a.lam = a.l_ag + a.via_p;
   return a;
 }
 
@@ -377,8 +358,7 @@ NB_HD __forceinline__ APRate ap_rate(double e_ag, double e_ap, double e_pg, doub
 NB_HD __forceinline__ double ap_dlog(const APRate& a, double g_ag, double g_ap, double g_pg,
                                      double g_pa) {
   if (!finite_nonzero(a.lam)) return g_ag;
-  const double inner = fma(1.0 - a.frac, g_pg - g_pa, g_ap);
-  return fma(a.l_ag, g_ag, mul_nc(a.via_p, inner)) / a.lam;
+  return (a.l_ag * g_ag + a.via_p * (g_ap + (1.0 - a.frac) * (g_pg - g_pa))) / a.lam;
 }
 
 // Rates near a reference temperature.  Within one step attempt T9 moves
