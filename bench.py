@@ -77,9 +77,6 @@ def kernel_source_hash() -> str:
     for f in KERNEL_SOURCES:
         with open(os.path.join(d, f), "rb") as fh:
             h.update(fh.read())
-    # and the compiler flags
-    with open(os.path.join(ROOT, "paper_2312_02836_gb300", "build.py"), "rb") as fh:
-        h.update(fh.read())
     return h.hexdigest()[:16]
 
 

@@ -65,7 +65,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     _write_embedded()
     nvcc = os.environ.get("NVCC", "nvcc")
-    common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-fmad=true", "-Xcompiler", "-fPIC",
+    common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC",
                      "-I", os.path.join(HERE, "..", "include"), "-I", BUILD]
     procs, objs = [], []
     for src in SOURCES:
