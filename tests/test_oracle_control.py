@@ -270,3 +270,18 @@ def test_controller_decisions_replayed_exactly(name, zone):
     assert checked >= 0.8 * (len(tp["t"]) - 3)
     if name in ("bateman", "net48"):
         assert "up" in changes
+
+
+@pytest.mark.parametrize("name,zone", [("chain13_heat", 0), ("net48", 1)])
+def test_order_sum_counter_is_the_sum_of_the_taped_orders(name, zone):
+    # the ninth counter fingerprints the path: the orders of the accepted
+    # steps, summed, as the tape records them (record 0 is the start)
+    import gen
+    net, z, st = gen.problem(name, zone + 1)
+    tp = oracle.burn_tape(net, z["Y"][zone], z["T9"][zone], z["rho"][zone], st["t_end"],
+                          st["rtol"], st["atol"])
+    assert tp["status"] == 0
+    cnt = np.asarray(tp["counters"]).reshape(-1)
+    assert cnt[0] == len(tp["k"]) - 1
+    assert cnt[8] == int(np.sum(tp["k"][1:]))
+    assert 1 <= tp["k"][1:].min() and tp["k"][1:].max() <= 5

@@ -98,3 +98,27 @@ def test_status_may_differ_only_where_rounding_decides_it():
     spread["status_sensitive"][3] = True
     rep = compare(g, o, s["atol"], spread=spread)
     assert rep["status_differs_rounding_decided"] == [3]
+
+
+def test_a_failed_zone_is_rounding_decided_when_variants_fail_elsewhere():
+    # a zone the oracle ends with a failure status counts as decided by
+    # rounding when a variant fails it after more than 2 steps more or less,
+    # and only then (synthetic results: statuses and counts are what matter)
+    Z, N = 4, 3
+    base = dict(Y=np.full((Z, N), 0.1), T9=np.ones(Z), E=np.zeros(Z),
+                counters=np.tile(np.arange(1, 10, dtype=np.int32) * 100, (Z, 1)),
+                status=np.array([0, 2, 2, 3], dtype=np.int32))
+    var = {k: np.array(v, copy=True) for k, v in base.items()}
+    var["counters"][1, 0] += 3      # fails 3 steps later: rounding-decided
+    var["counters"][2, 0] += 2      # fails 2 steps later: within the step bar
+    var["counters"][0, 0] += 5      # an OK zone with another count: diverged, not this rule
+    sp = oracle_spread(base, [var], 1e-12, 1e-8)
+    assert sp["status_sensitive"].tolist() == [False, True, False, False]
+    # the GPU may then end zone 1 OK; zone 2 or 3 may not
+    g = {k: np.array(v, copy=True) for k, v in base.items()}
+    g["status"][1] = 0
+    rep = compare(g, base, 1e-12, spread=sp)
+    assert rep["rounding_decided_zones"] == [1]
+    g["status"][2] = 0
+    with pytest.raises(AssertionError):
+        compare(g, base, 1e-12, spread=sp)
