@@ -16,6 +16,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -71,12 +72,21 @@ KERNEL_SOURCES = ("integrator.cuh", "expf64.cuh", "blob.h", "device.cuh", "netlo
                   "codegen.cpp", "burn.cu", "coop.cuh", "adjoint.cuh", "adjoint.cu")
 
 
+def _code_only(text: str) -> str:
+    """C++ source without its comments and blank lines (what a comment edit
+    leaves unchanged).  Text after a // inside a string literal goes too; in
+    these sources that is only the text of generated comments."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    lines = (re.sub(r"//.*", "", line).rstrip() for line in text.splitlines())
+    return "\n".join(line for line in lines if line)
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2312_02836_gb300", "csrc")
     for f in KERNEL_SOURCES:
-        with open(os.path.join(d, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(d, f), encoding="utf-8") as fh:
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

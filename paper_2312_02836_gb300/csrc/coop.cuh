@@ -1,5 +1,6 @@
-// coop.cuh -- one zone per warp: the network evaluation of the integrator
-// (integrator.cuh) spread over the 32 lanes of a warp, for large networks.
+// coop.cuh -- one zone per warp (or per block of two or four warps, see
+// WNetT): the network evaluation of the integrator (integrator.cuh) spread
+// over the team's threads, for large networks.
 //
 // On this GPU an FP64 warp instruction costs the FP64 pipe the same time
 // whatever its active lanes, so one lane per zone keeps the pipe busiest

@@ -26,11 +26,12 @@
 // straight-line code with every index a constant and compiled at run time.
 // Both run one zone per lane and perform the same floating-point operations
 // in the same order, so they give the same bits.  The cooperative one
-// (coop.cuh) runs one zone per warp: its vector loops are spread over the
-// 32 lanes (vbeg/vstep), its sums are warp reductions (vsum) and its phases
-// are separated by warp barriers (vsync); every lane holds the same copy of
-// the zone's scalars, so control flow stays uniform.  For the one-zone-per-
-// lane types these helpers reduce to the plain loops and do nothing.
+// (coop.cuh) runs one zone per team of W threads, a warp or a block of two
+// or four warps: its vector loops are spread over the team (vbeg/vstep),
+// its sums are team reductions (vsum) and its phases are separated by the
+// team's barriers (vsync); every thread holds the same copy of the zone's
+// scalars, so control flow stays uniform.  For the one-zone-per-lane types
+// these helpers reduce to the plain loops and do nothing.
 //
 // This header is also compiled by the run-time compiler, so it includes no
 // system header.
